@@ -1,0 +1,556 @@
+// CPU oracle for exact treewidth by breadth-first elimination-ordering DP.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+// CUDA path is checked against.  Only the test suite, the smoke check and the
+// CPU-baseline leg of the benchmark may load it; the product path never does.
+// It shares no code, header or constant table with the CUDA library.
+//
+// What it follows (van der Zanden & Bodlaender, "Computing Treewidth on the
+// GPU", arXiv 1709.09990):
+//   * Section 2 (Preliminaries): tw(G) = min over orderings pi of
+//     max over v of |Q({u : pi(u) < pi(v)}, v)|, where Q(S, v) is the set of
+//     vertices outside S reachable from v by a path whose interior lies in S.
+//   * Section 3.1, Listing 1: for k = 0, 1, ... start from the list {empty
+//     set}; for levels i = 0 .. n-k-2 extend every set S of the list by every
+//     vertex v not in S whose degree after eliminating S (a depth-first search
+//     over S) is at most k; the union of the extensions is the next list.  A
+//     non-empty list after the last level means tw <= k.  The last k+1
+//     vertices may be eliminated in any order (the third optimisation of
+//     Section 3.1), which is why the level range stops at n-k-1.
+//
+// Readings taken where the paper is silent or ambiguous:
+//   R1  v itself is marked visited before the search starts, so Q(S,v) never
+//       contains v (the definition takes simple paths to u in V \ S).
+//   R2  The listing's level range is canonical; a level that comes out empty
+//       ends the run (every later level would be empty too).
+//   R3  k >= n-1 answers yes with the single level {empty set}.
+//   R4  Sets are exact (the paper's Bloom filter is lossy); level sizes are
+//       the sizes of exact sets.
+//
+// Independent pins (exercised by tests/test_oracle_*.py):
+//   * brute force over all n! orderings with an explicit elimination game
+//     (remove v, turn its neighbourhood into a clique; Section 2, second
+//     paragraph) for n <= 10;
+//   * a subset DP over all 2^n masks that tracks the eliminated graph
+//     explicitly (fill-in edges) instead of the reachability search, n <= 22.
+//
+// Layout of every adjacency argument: n rows of W = ceil(n/64) little-endian
+// uint64 words; bit c of row r is set iff rc is an edge.  n <= 128.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+namespace {
+
+constexpr int kMaxN = 128;
+
+struct Key {
+  uint64_t w[2];
+  bool operator==(const Key& o) const { return w[0] == o.w[0] && w[1] == o.w[1]; }
+};
+
+// splitmix64 output function (Steele, Lea & Flood 2014), used as the set
+// fingerprint and as the hash of the unordered containers.
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Fingerprint of a vertex set: mix64(w0 ^ mix64(w1)).
+uint64_t set_fingerprint(const Key& s) { return mix64(s.w[0] ^ mix64(s.w[1])); }
+
+struct KeyHash {
+  size_t operator()(const Key& k) const { return (size_t)set_fingerprint(k); }
+};
+
+bool has(const Key& s, int v) { return (s.w[v >> 6] >> (v & 63)) & 1ULL; }
+Key with(Key s, int v) {
+  s.w[v >> 6] |= 1ULL << (v & 63);
+  return s;
+}
+Key without(Key s, int v) {
+  s.w[v >> 6] &= ~(1ULL << (v & 63));
+  return s;
+}
+
+struct Graph {
+  int n = 0;
+  std::vector<std::vector<int>> nbr;        // adjacency lists, increasing order
+  std::vector<std::vector<char>> mat;       // adjacency matrix
+};
+
+int words_for(int n) { return n <= 64 ? 1 : (n + 63) / 64; }
+
+// Returns false on an invalid graph (asymmetric row, self-loop, bits >= n).
+bool load_graph(const uint64_t* adj, int n, Graph* g) {
+  if (n < 1 || n > kMaxN || adj == nullptr) return false;
+  const int W = words_for(n);
+  g->n = n;
+  g->nbr.assign(n, {});
+  g->mat.assign(n, std::vector<char>(n, 0));
+  for (int r = 0; r < n; ++r) {
+    for (int c = 0; c < W * 64; ++c) {
+      const bool bit = (adj[(size_t)r * W + (c >> 6)] >> (c & 63)) & 1ULL;
+      if (!bit) continue;
+      if (c >= n || c == r) return false;
+      g->mat[r][c] = 1;
+    }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      if (g->mat[r][c] != g->mat[c][r]) return false;
+      if (g->mat[r][c]) g->nbr[r].push_back(c);
+    }
+  return true;
+}
+
+// Listing 1, the inner search: the degree of v in the graph that remains after
+// eliminating S, found by a depth-first search from v through S.  Every
+// first-time-seen vertex outside S adds one.  Reading R1: v starts visited.
+int dfs_degree(const Graph& g, const Key& S, int v) {
+  char visited[kMaxN];
+  int stack[kMaxN + 1];
+  std::memset(visited, 0, sizeof(visited));
+  int top = 0;
+  int degree = 0;
+  visited[v] = 1;
+  stack[top++] = v;
+  while (top > 0) {
+    const int u = stack[--top];
+    for (int w : g.nbr[u]) {
+      if (visited[w]) continue;
+      visited[w] = 1;
+      if (has(S, w))
+        stack[top++] = w;
+      else
+        ++degree;
+    }
+  }
+  return degree;
+}
+
+// Q(S, v) itself (same search, collecting the vertices instead of counting).
+Key q_set(const Graph& g, const Key& S, int v) {
+  char visited[kMaxN];
+  int stack[kMaxN + 1];
+  std::memset(visited, 0, sizeof(visited));
+  Key q{{0, 0}};
+  int top = 0;
+  visited[v] = 1;
+  stack[top++] = v;
+  while (top > 0) {
+    const int u = stack[--top];
+    for (int w : g.nbr[u]) {
+      if (visited[w]) continue;
+      visited[w] = 1;
+      if (has(S, w))
+        stack[top++] = w;
+      else
+        q = with(q, w);
+    }
+  }
+  return q;
+}
+
+int popcount_key(const Key& s) { return __builtin_popcountll(s.w[0]) + __builtin_popcountll(s.w[1]); }
+
+struct DecideOut {
+  int yes = 0;
+  int levels = 0;
+  std::vector<int64_t> level_size;
+  std::vector<uint64_t> fp_sum, fp_xor;
+  int64_t states_expanded = 0;
+  int64_t candidates = 0;
+  int64_t feasible = 0;
+  std::vector<int> order;  // filled when want_order and yes
+};
+
+// Listing 1 for one value of k, with exact sets (reading R4).
+void decide(const Graph& g, int k, bool want_order, DecideOut* out) {
+  const int n = g.n;
+  out->level_size.assign(n + 1, 0);
+  out->fp_sum.assign(n + 1, 0);
+  out->fp_xor.assign(n + 1, 0);
+  out->order.clear();
+
+  // Each level maps a set to one predecessor vertex (the v that first
+  // produced it); level 0 holds the empty set.
+  std::vector<std::unordered_map<Key, int, KeyHash>> kept;
+  std::unordered_map<Key, int, KeyHash> inp;
+  inp.emplace(Key{{0, 0}}, -1);
+  out->level_size[0] = 1;
+  out->fp_sum[0] = set_fingerprint(Key{{0, 0}});
+  out->fp_xor[0] = out->fp_sum[0];
+  int last = 0;
+
+  for (int i = 0; i <= n - k - 2; ++i) {
+    std::unordered_map<Key, int, KeyHash> outp;
+    for (const auto& entry : inp) {
+      const Key& S = entry.first;
+      for (int v = 0; v < n; ++v) {
+        if (has(S, v)) continue;
+        ++out->candidates;
+        const int degree = dfs_degree(g, S, v);
+        if (degree <= k) {
+          ++out->feasible;
+          outp.emplace(with(S, v), v);  // keeps the first predecessor
+        }
+      }
+    }
+    out->states_expanded += (int64_t)inp.size();
+    if (want_order) kept.push_back(std::move(inp));
+    inp = std::move(outp);
+    last = i + 1;
+    out->level_size[last] = (int64_t)inp.size();
+    uint64_t s = 0, x = 0;
+    for (const auto& entry : inp) {
+      const uint64_t f = set_fingerprint(entry.first);
+      s += f;
+      x ^= f;
+    }
+    out->fp_sum[last] = s;
+    out->fp_xor[last] = x;
+    if (inp.empty()) break;  // reading R2
+  }
+  out->levels = last + 1;
+  out->yes = inp.empty() ? 0 : 1;
+
+  if (want_order && out->yes) {
+    // Walk back from any final set through the recorded predecessors.
+    Key S = inp.begin()->first;
+    const Key final_set = S;
+    std::vector<int> prefix(last, -1);
+    for (int j = last; j >= 1; --j) {
+      const auto& level = (j == last) ? inp : kept[j];
+      const int v = level.at(S);
+      prefix[j - 1] = v;
+      S = without(S, v);
+    }
+    out->order = prefix;
+    for (int v = 0; v < n; ++v)
+      if (!has(final_set, v)) out->order.push_back(v);
+  }
+}
+
+// Width of an ordering through Q (Section 2's definition).
+int width_by_q(const Graph& g, const int* order) {
+  const int n = g.n;
+  std::vector<char> seen(n, 0);
+  for (int j = 0; j < n; ++j) {
+    if (order[j] < 0 || order[j] >= n || seen[order[j]]) return -1;
+    seen[order[j]] = 1;
+  }
+  Key prefix{{0, 0}};
+  int width = 0;
+  for (int j = 0; j < n; ++j) {
+    const int v = order[j];
+    width = std::max(width, dfs_degree(g, prefix, v));
+    prefix = with(prefix, v);
+  }
+  return width;
+}
+
+// Width of an ordering by the explicit elimination game: remove v, turn its
+// remaining neighbourhood into a clique (Section 2, second paragraph).
+int width_by_elimination(const Graph& g, const int* order) {
+  const int n = g.n;
+  std::vector<std::vector<char>> m = g.mat;
+  std::vector<char> gone(n, 0);
+  int width = 0;
+  for (int j = 0; j < n; ++j) {
+    const int v = order[j];
+    if (v < 0 || v >= n || gone[v]) return -1;
+    std::vector<int> nb;
+    for (int u = 0; u < n; ++u)
+      if (!gone[u] && u != v && m[v][u]) nb.push_back(u);
+    width = std::max(width, (int)nb.size());
+    for (int a : nb)
+      for (int b : nb)
+        if (a != b) m[a][b] = 1;
+    gone[v] = 1;
+  }
+  return width;
+}
+
+}  // namespace
+
+extern "C" {
+
+int orc_max_n() { return kMaxN; }
+
+uint64_t orc_set_fingerprint(uint64_t w0, uint64_t w1) { return set_fingerprint(Key{{w0, w1}}); }
+
+// Validates an adjacency: 1 if it is a simple undirected graph, else 0.
+int orc_valid_graph(const uint64_t* adj, int n) {
+  Graph g;
+  return load_graph(adj, n, &g) ? 1 : 0;
+}
+
+// |Q(S, v)| through the Listing-1 search.  S is given as two words.
+int orc_q_size(const uint64_t* adj, int n, uint64_t s0, uint64_t s1, int v) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || v < 0 || v >= n) return -1;
+  return dfs_degree(g, Key{{s0, s1}}, v);
+}
+
+// Q(S, v) as two words.
+int orc_q_set(const uint64_t* adj, int n, uint64_t s0, uint64_t s1, int v, uint64_t* q_out) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || v < 0 || v >= n) return -1;
+  const Key q = q_set(g, Key{{s0, s1}}, v);
+  q_out[0] = q.w[0];
+  q_out[1] = q.w[1];
+  return 0;
+}
+
+// One run of Listing 1 at bound k.  Arrays level_size / fp_sum / fp_xor have
+// n+1 entries (entries past the last level are zero).  counters[0..2] =
+// states expanded, candidates, feasible candidates.  order (n entries, or
+// NULL) receives an elimination ordering of width <= k when the answer is
+// yes.  Returns 1 (yes), 0 (no) or -1 (invalid input).
+int orc_decide(const uint64_t* adj, int n, int k, int64_t* level_size, uint64_t* fp_sum,
+               uint64_t* fp_xor, int* levels, int64_t* counters, int32_t* order) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || k < 0) return -1;
+  DecideOut out;
+  decide(g, k, order != nullptr, &out);
+  for (int i = 0; i <= n; ++i) {
+    if (level_size) level_size[i] = out.level_size[i];
+    if (fp_sum) fp_sum[i] = out.fp_sum[i];
+    if (fp_xor) fp_xor[i] = out.fp_xor[i];
+  }
+  if (levels) *levels = out.levels;
+  if (counters) {
+    counters[0] = out.states_expanded;
+    counters[1] = out.candidates;
+    counters[2] = out.feasible;
+  }
+  if (order && out.yes)
+    for (int j = 0; j < n; ++j) order[j] = out.order[j];
+  return out.yes;
+}
+
+// Iterative deepening (Listing 1, outer loop) from k_start upward; the first
+// yes is the treewidth.  counters[0..2] are summed over every k tried;
+// counters[3] = number of k tried.  Returns tw or -1.
+int orc_solve(const uint64_t* adj, int n, int k_start, int32_t* order, int64_t* counters) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || k_start < 0) return -1;
+  int64_t tot[4] = {0, 0, 0, 0};
+  for (int k = k_start; k < n; ++k) {
+    DecideOut out;
+    decide(g, k, order != nullptr, &out);
+    tot[0] += out.states_expanded;
+    tot[1] += out.candidates;
+    tot[2] += out.feasible;
+    tot[3] += 1;
+    if (out.yes) {
+      if (order)
+        for (int j = 0; j < n; ++j) order[j] = out.order[j];
+      if (counters) std::memcpy(counters, tot, sizeof(tot));
+      return k;
+    }
+  }
+  return -1;  // unreachable for a valid graph: k = n-1 always answers yes
+}
+
+// Width of an ordering via Q; -1 if order is not a permutation of 0..n-1.
+int orc_width_q(const uint64_t* adj, int n, const int32_t* order) {
+  Graph g;
+  if (!load_graph(adj, n, &g)) return -1;
+  std::vector<int> o(order, order + n);
+  return width_by_q(g, o.data());
+}
+
+// Width of an ordering via the elimination game.
+int orc_width_elim(const uint64_t* adj, int n, const int32_t* order) {
+  Graph g;
+  if (!load_graph(adj, n, &g)) return -1;
+  std::vector<int> o(order, order + n);
+  return width_by_elimination(g, o.data());
+}
+
+// Brute force over all n! orderings (elimination game), n <= 10.
+int orc_brute_force_tw(const uint64_t* adj, int n) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || n > 10) return -1;
+  std::vector<int> perm(n);
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  int best = n;
+  do {
+    best = std::min(best, width_by_elimination(g, perm.data()));
+  } while (std::next_permutation(perm.begin(), perm.end()));
+  return best;
+}
+
+// Subset DP over all 2^n vertex masks, n <= 22, independent of the search
+// above: it keeps, for every feasible mask S, the graph that remains after
+// eliminating S (adjacency rows over V \ S with fill-in edges), built by
+// eliminating one vertex at a time.  feasible[S u {v}] holds iff S is feasible
+// and v has degree <= k in that graph.  Reports the sizes and fingerprints of
+// the levels 0 .. n-k-1 with the same truncation at the first empty level.
+// Returns 1/0 (yes/no) or -1.
+int orc_subset_dp(const uint64_t* adj, int n, int k, int64_t* level_size, uint64_t* fp_sum,
+                  uint64_t* fp_xor, int* levels) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || n > 22 || k < 0) return -1;
+  const uint32_t full = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  const size_t masks = (size_t)1 << n;
+  std::vector<uint8_t> feasible(masks, 0);
+  // rows[mask * n + u] = neighbours of u in the graph after eliminating mask.
+  std::vector<uint32_t> rows(masks * (size_t)n, 0);
+  std::vector<uint8_t> built(masks, 0);
+  for (int u = 0; u < n; ++u) {
+    uint32_t r = 0;
+    for (int v : g.nbr[u]) r |= 1u << v;
+    rows[u] = r;
+  }
+  built[0] = 1;
+  feasible[0] = 1;
+  const int top_level = std::max(0, n - k - 1);
+  for (size_t m = 0; m < masks; ++m) {
+    if (!feasible[m]) continue;
+    const int pc = __builtin_popcount((uint32_t)m);
+    if (pc >= top_level) continue;
+    const uint32_t* R = &rows[m * n];
+    for (int v = 0; v < n; ++v) {
+      if ((m >> v) & 1u) continue;
+      const int deg = __builtin_popcount(R[v]);
+      if (deg > k) continue;
+      const size_t m2 = m | ((size_t)1 << v);
+      feasible[m2] = 1;
+      if (!built[m2]) {
+        // Eliminate v from the graph of m: its neighbourhood becomes a clique.
+        uint32_t* R2 = &rows[m2 * n];
+        const uint32_t nb = R[v];
+        for (int u = 0; u < n; ++u) {
+          if ((m2 >> u) & 1u) {
+            R2[u] = 0;
+            continue;
+          }
+          uint32_t r = R[u] & ~(1u << v);
+          if ((nb >> u) & 1u) r |= nb & ~(1u << u);
+          R2[u] = r & full;
+        }
+        built[m2] = 1;
+      }
+    }
+  }
+  std::vector<int64_t> cnt(n + 1, 0);
+  std::vector<uint64_t> fs(n + 1, 0), fx(n + 1, 0);
+  for (size_t m = 0; m < masks; ++m) {
+    if (!feasible[m]) continue;
+    const int pc = __builtin_popcount((uint32_t)m);
+    if (pc > top_level) continue;
+    cnt[pc] += 1;
+    const uint64_t f = set_fingerprint(Key{{(uint64_t)m, 0}});
+    fs[pc] += f;
+    fx[pc] ^= f;
+  }
+  int last = 0;
+  while (last < top_level && cnt[last + 1] > 0) ++last;
+  if (last < top_level) ++last;  // include the first empty level
+  for (int i = 0; i <= n; ++i) {
+    const bool in = i <= last;
+    if (level_size) level_size[i] = in ? cnt[i] : 0;
+    if (fp_sum) fp_sum[i] = in ? fs[i] : 0;
+    if (fp_xor) fp_xor[i] = in ? fx[i] : 0;
+  }
+  if (levels) *levels = last + 1;
+  return cnt[top_level] > 0 ? 1 : 0;
+}
+
+// Tree decomposition from an ordering: bag(v) = {v} u Q(prefix(v), v);
+// parent(v) = the vertex of Q(prefix(v), v) that comes first in the order
+// after v; a vertex with empty Q hangs below the last vertex of the order,
+// which is the root (parent -1).  bags: n rows of W words.  Returns the width.
+int orc_td_from_order(const uint64_t* adj, int n, const int32_t* order, int32_t* parent,
+                      uint64_t* bags) {
+  Graph g;
+  if (!load_graph(adj, n, &g)) return -1;
+  const int W = words_for(n);
+  std::vector<int> pos(n, -1);
+  for (int j = 0; j < n; ++j) {
+    if (order[j] < 0 || order[j] >= n || pos[order[j]] >= 0) return -1;
+    pos[order[j]] = j;
+  }
+  Key prefix{{0, 0}};
+  int width = 0;
+  for (int j = 0; j < n; ++j) {
+    const int v = order[j];
+    const Key q = q_set(g, prefix, v);
+    const Key bag = with(q, v);
+    for (int w = 0; w < W; ++w) bags[(size_t)v * W + w] = bag.w[w];
+    width = std::max(width, popcount_key(bag) - 1);
+    int best = -1;
+    for (int u = 0; u < n; ++u)
+      if (has(q, u) && (best < 0 || pos[u] < pos[best])) best = u;
+    if (best < 0) best = (j == n - 1) ? -1 : order[n - 1];
+    parent[v] = best;
+    prefix = with(prefix, v);
+  }
+  return width;
+}
+
+// Checks a tree decomposition given as one bag per vertex plus parent
+// pointers: the parent pointers form a single rooted tree, every vertex lies
+// in a bag, every edge lies in a bag, and for every vertex x the bags holding
+// x are connected in the tree.  Returns the width, or -1 if any check fails.
+int orc_verify_td(const uint64_t* adj, int n, const int32_t* parent, const uint64_t* bags) {
+  Graph g;
+  if (!load_graph(adj, n, &g)) return -1;
+  const int W = words_for(n);
+  auto in_bag = [&](int b, int x) { return (bags[(size_t)b * W + (x >> 6)] >> (x & 63)) & 1ULL; };
+  int roots = 0;
+  for (int b = 0; b < n; ++b) {
+    if (parent[b] == -1)
+      ++roots;
+    else if (parent[b] < 0 || parent[b] >= n || parent[b] == b)
+      return -1;
+  }
+  if (roots != 1) return -1;
+  // Acyclic: every node reaches the root within n steps.
+  for (int b = 0; b < n; ++b) {
+    int c = b, steps = 0;
+    while (parent[c] != -1) {
+      c = parent[c];
+      if (++steps > n) return -1;
+    }
+  }
+  for (int x = 0; x < n; ++x) {
+    bool found = false;
+    for (int b = 0; b < n && !found; ++b) found = in_bag(b, x);
+    if (!found) return -1;
+  }
+  for (int u = 0; u < n; ++u)
+    for (int v : g.nbr[u]) {
+      bool found = false;
+      for (int b = 0; b < n && !found; ++b) found = in_bag(b, u) && in_bag(b, v);
+      if (!found) return -1;
+    }
+  // Running intersection: among the bags holding x exactly one has a parent
+  // that does not hold x (or is the root).
+  for (int x = 0; x < n; ++x) {
+    int tops = 0;
+    for (int b = 0; b < n; ++b) {
+      if (!in_bag(b, x)) continue;
+      if (parent[b] == -1 || !in_bag(parent[b], x)) ++tops;
+    }
+    if (tops != 1) return -1;
+  }
+  int width = 0;
+  for (int b = 0; b < n; ++b) {
+    int c = 0;
+    for (int x = 0; x < n; ++x) c += in_bag(b, x) ? 1 : 0;
+    width = std::max(width, c - 1);
+  }
+  return width;
+}
+
+}  // extern "C"
