@@ -1,0 +1,192 @@
+/*
+ * tw.h - C ABI of libtw, exact treewidth on one GB300 GPU (sm_103a).
+ *
+ * Method: van der Zanden & Bodlaender, "Computing Treewidth on the GPU"
+ * (arXiv 1709.09990).
+ *   Section 2: tw(G) = min over elimination orderings pi of
+ *     max_v |Q({u : pi(u) < pi(v)}, v)|, where Q(S, v) is the set of vertices
+ *     outside S u {v} reachable from v by a path whose interior lies in S.
+ *   Section 3.1, Listing 1: decide(k) grows the wavefront level by level:
+ *     L_0 = {empty set}; L_{i+1} = { S u {v} : S in L_i, v not in S,
+ *     |Q(S,v)| <= k }, for i = 0 .. n-k-2; tw <= k iff L_{n-k-1} is not empty
+ *     (the last k+1 vertices can be eliminated in any order).  The treewidth
+ *     is the first k that answers yes.
+ *   Section 3.2: duplicate sets are removed; here with an exact device hash
+ *     table (the paper's Bloom filter can lose states and is not used).
+ *   Section 3.1, last paragraph: the paper does not reconstruct orderings;
+ *     libtw keeps one predecessor vertex per state and walks back.
+ *
+ * Conventions shared by every entry point
+ *   Adjacency ("adj"): n rows, each W = ceil(n/64) little-endian uint64
+ *     words; bit c of row r is set iff rc is an edge.  The graph must be
+ *     simple and undirected: symmetric rows, zero diagonal, no bit >= n.
+ *     1 <= n <= TW_MAX_N.  Anything else returns TW_ERR_INVALID.
+ *   Pointers: every array argument may be host memory or device memory of
+ *     the context's device (libtw asks the driver which one it is).  The
+ *     caller owns all memory; libtw copies inputs before working and writes
+ *     outputs before returning; it keeps no pointer after a call returns.
+ *   Results are exact.  When the frontier or table would exceed the memory
+ *     cap the call returns TW_ERR_CAPACITY and gives no answer; no state is
+ *     ever dropped.
+ *   A context is bound to one device and one stream and is not thread safe:
+ *     use one context per host thread.
+ */
+#ifndef TW_H
+#define TW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TW_MAX_N 128
+#define TW_ABI_VERSION 1
+
+/* Status codes. */
+#define TW_OK 0
+#define TW_ERR_INVALID 1  /* bad graph, n, k or NULL required pointer        */
+#define TW_ERR_CAPACITY 2 /* frontier or table would exceed the memory cap   */
+#define TW_ERR_TIMEOUT 3  /* a bounded device wait expired                   */
+#define TW_ERR_CUDA 4     /* a CUDA runtime call failed                      */
+
+typedef struct tw_ctx tw_ctx;
+
+/* Context configuration; an all-zero struct selects every default. */
+typedef struct {
+  int device;             /* CUDA device ordinal                                  */
+  int fingerprints;       /* 1: fill level_fp_sum / level_fp_xor in tw_stats     */
+  size_t mem_cap_bytes;   /* device bytes libtw may hold; 0 = 150 GB or 90% free  */
+  void* stream;           /* cudaStream_t to run on; NULL = a stream of libtw's  */
+  int block_threads;      /* expand kernel block size; 0 = autotuned/default     */
+  int table_load_pct;     /* hash table target load in percent; 0 = default (50) */
+  int max_probes;         /* probe limit per insert; 0 = default (cap of table)  */
+  int ub_shortcut;        /* tw_solve: accept the heuristic upper bound when the
+                             lower bound meets it, without a decide run (0 = off) */
+  int graph_levels;       /* 1 = drive levels through a captured CUDA graph       */
+  int reserved[7];        /* must be zero                                         */
+} tw_config;
+
+/* Per-call statistics.  Level arrays describe the last decide run. */
+typedef struct {
+  int levels;                               /* levels computed (incl. L_0)     */
+  int k;                                    /* bound of the last decide run    */
+  uint64_t level_size[TW_MAX_N + 1];        /* |L_i|                            */
+  uint64_t level_fp_sum[TW_MAX_N + 1];      /* sum of fp(S) over L_i (mod 2^64) */
+  uint64_t level_fp_xor[TW_MAX_N + 1];      /* xor of fp(S) over L_i            */
+  uint64_t states_expanded;                 /* sum of |L_i| over expanded levels,
+                                               summed over every decide run    */
+  uint64_t candidates;                      /* sum of |L_i| * (n - i), likewise */
+  uint64_t feasible;                        /* candidates with |Q| <= k         */
+  uint64_t peak_frontier_bytes;             /* max over levels of kept lists +
+                                               live table bytes                 */
+  uint64_t decide_runs;                     /* decide runs in this call         */
+  uint64_t level_retries;                   /* levels re-run after growing      */
+  double seconds;                           /* wall time of the call            */
+} tw_stats;
+
+/* fp(S) = mix(w0 ^ mix(w1)), mix = the splitmix64 output function, over the
+ * two low words of S (zero-extended).  Used only for the level fingerprints. */
+
+/* Creates a context on cfg->device.  cfg may be NULL (defaults).
+ * Errors: TW_ERR_INVALID (out NULL, nonzero reserved), TW_ERR_CUDA. */
+int tw_create(tw_ctx** out, const tw_config* cfg);
+
+/* Frees every device buffer of the context.  NULL is ignored. */
+void tw_destroy(tw_ctx* ctx);
+
+/* Listing 1 at bound k (arXiv 1709.09990, Section 3.1).
+ *   adj   : n x ceil(n/64) uint64 rows (see conventions).
+ *   k     : the bound, k >= 0.  k >= n-1 answers yes without expansion.
+ *   yes   : out, 1 if tw <= k, else 0.
+ *   order : out, n int32 (or NULL): on yes, an elimination ordering of width
+ *           <= k (order[j] = the j-th vertex eliminated); untouched on no.
+ *   st    : out statistics (or NULL).
+ * Returns TW_OK or an error status; on error nothing is written to yes/order. */
+int tw_decide(tw_ctx* ctx, const uint64_t* adj, int n, int k, int* yes, int32_t* order,
+              tw_stats* st);
+
+/* As tw_decide for n <= 32 with one uint32 word per row (bit c of row r =
+ * edge rc).  Runs the 32-bit state kernel. */
+int tw_decide_u32(tw_ctx* ctx, const uint32_t* adj_rows, int n, int k, int* yes,
+                  int32_t* order, tw_stats* st);
+
+/* Exact treewidth: decide(k) for k = LB, LB+1, ... where LB = max(minimum-
+ * degree bound, minor-min-width bound); the first yes is tw (Section 3.1,
+ * iterative deepening).
+ *   tw        : out, the treewidth.
+ *   order     : out, n int32 (or NULL), an ordering of width tw.
+ *   td_parent : out, n int32 (or NULL): bag of vertex v hangs below the bag of
+ *               td_parent[v]; exactly one root has -1.
+ *   td_bags   : out, n rows x ceil(n/64) uint64 (or NULL): bag of v =
+ *               {v} u Q(prefix(v), v).  td_* need order's walk, so they are
+ *               filled only when order or the td arrays are requested.
+ *   st        : out (or NULL); level arrays describe the final (yes) run.   */
+int tw_solve(tw_ctx* ctx, const uint64_t* adj, int n, int* tw, int32_t* order,
+             int32_t* td_parent, uint64_t* td_bags, tw_stats* st);
+
+/* Many graphs of uneven size in one level-synchronous batched run.
+ *   adj_concat : the graphs' rows concatenated; graph g starts at word
+ *                row_offset[g] and has n[g] rows of ceil(n[g]/64) words.
+ *   n          : num_graphs vertex counts (1 .. 64 for the batched kernel;
+ *                larger graphs are solved one at a time).
+ *   tw         : out, num_graphs treewidths (-1 where status != TW_OK).
+ *   orders     : out (or NULL), concatenated orderings; graph g's starts at
+ *                the prefix sum of n[0..g-1].
+ *   status     : out, num_graphs per-graph status.
+ *   k_hint     : NULL for the plain sweep from the lower bound, else
+ *                num_graphs proposed starting bounds: decide runs at
+ *                round(k_hint) and round(k_hint)-1 and walks up or down from
+ *                there until the answer is certified (yes at tw, no at tw-1).
+ *   st         : out (or NULL): totals over all graphs.
+ * Returns the worst per-graph status. */
+int tw_solve_batch(tw_ctx* ctx, const uint64_t* adj_concat, const int32_t* n,
+                   const int64_t* row_offset, int num_graphs, int* tw, int32_t* orders,
+                   int* status, const float* k_hint, tw_stats* st);
+
+/* Lower and upper bounds on the device (one warp per graph):
+ * out[0] = minimum-degree (degeneracy) bound, out[1] = minor-min-width
+ * (MMD+, Section 3.3), out[2] = width of the greedy minimum-degree ordering,
+ * out[3] = width of the greedy minimum-fill ordering.  Ties: lowest index. */
+int tw_bounds(tw_ctx* ctx, const uint64_t* adj, int n, int32_t out[4]);
+
+/* The 12 features of the learned starting bound for many graphs (same
+ * concatenated layout as tw_solve_batch), one warp per graph, fp32:
+ * 0 n/64; 1 density; 2-5 min/max/mean/std degree over n; 6-9 fraction of
+ * vertices with degree/n in [0,.25), [.25,.5), [.5,.75), [.75,1];
+ * 10 MMD+/n; 11 (min-degree width + min-fill width)/(2n).
+ *   feats : out, num_graphs x 12 float (row-major). */
+int tw_features_batch(tw_ctx* ctx, const uint64_t* adj_concat, const int32_t* n,
+                      const int64_t* row_offset, int num_graphs, float* feats);
+
+/* The 12-32-1 ReLU network that proposes a starting bound (no counterpart in
+ * the paper; every answer it leads to is still certified by decide runs).
+ * Parameters: 449 float, W1 [32][12] row-major, b1[32], W2[32], b2.
+ *   tw_mlp_forward : yhat[b] = W2 . relu(W1 x_b + b1) + b2 for b < batch.
+ *   tw_mlp_grad    : grad (449 float) of (1/B) sum_b (yhat_b - y_b)^2.
+ *   tw_mlp_adam    : one Adam step (Kingma & Ba) in place on params, m, v at
+ *                    step t >= 1 with the given hyper-parameters.
+ *   tw_mlp_train   : epochs of minibatch Adam over (x, y); perm holds
+ *                    epochs x batch_total sample indices (the random order is
+ *                    drawn by the caller); loss_out (epochs floats, or NULL)
+ *                    gets the mean training loss of each epoch. */
+int tw_mlp_forward(tw_ctx* ctx, const float* params, const float* x, int batch, float* yhat);
+int tw_mlp_grad(tw_ctx* ctx, const float* params, const float* x, const float* y, int batch,
+                float* grad);
+int tw_mlp_adam(tw_ctx* ctx, float* params, const float* grad, float* m, float* v, int t,
+                float lr, float beta1, float beta2, float eps);
+int tw_mlp_train(tw_ctx* ctx, float* params, const float* x, const float* y, int batch_total,
+                 int minibatch, int epochs, const int32_t* perm, float lr, float* loss_out);
+
+/* Human-readable name of a status code (static storage). */
+const char* tw_strerror(int status);
+
+/* ABI version (TW_ABI_VERSION of the library that was loaded). */
+int tw_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TW_H */

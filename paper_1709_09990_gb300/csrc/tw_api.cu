@@ -1,0 +1,919 @@
+// C ABI of libtw and the host drivers around the kernels.
+//
+// decide(k) follows Listing 1 of arXiv 1709.09990 (Section 3.1): L_0 = {{}},
+// one expansion per level i = 0 .. n-k-2, stop early at an empty level, and
+// answer yes iff L_{n-k-1} is not empty.  solve() is the iterative deepening
+// of the same section, started at a lower bound instead of 0 (the first yes
+// is the same k).
+//
+// Memory.  Every level's keys and predecessor bytes are kept in one growing
+// device arena when an ordering is wanted (the backward walk reads them);
+// otherwise only the current and the next level are live.  The hash table of
+// the level being built is a second buffer.  Nothing exceeds the context's
+// memory cap: a level that does not fit ends the call with TW_ERR_CAPACITY.
+// A level whose table or output list turns out too small is cleared and run
+// again with larger buffers, so no state is ever lost.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/tw.h"
+#include "tw_internal.h"
+
+using namespace tw;
+
+namespace {
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t mem_cap = 0;
+  tw_config cfg{};
+  DevBuf keys, pred, table, small;  // small: adjacency, walk, order, td scratch
+  DevBuf scratch;                    // staged batch inputs/outputs and network data
+  LevelCounters* d_ctr = nullptr;
+  LevelCounters* h_ctr = nullptr;
+  int sms = 0;
+};
+
+namespace {
+
+constexpr size_t kSmallBytes = 1 << 20;
+
+#define TW_CK(expr)                              \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) {                     \
+      cudaGetLastError();                        \
+      return TW_ERR_CUDA;                        \
+    }                                            \
+  } while (0)
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double seconds() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copies bytes from a host or device pointer into host memory.
+int fetch(void* dst_host, const void* src, size_t bytes) {
+  if (bytes == 0) return TW_OK;
+  if (is_device_ptr(src)) {
+    TW_CK(cudaMemcpy(dst_host, src, bytes, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(dst_host, src, bytes);
+  }
+  return TW_OK;
+}
+
+// Writes bytes from host memory to a host or device pointer.
+int put(tw_ctx* c, void* dst, const void* src_host, size_t bytes) {
+  if (bytes == 0 || dst == nullptr) return TW_OK;
+  if (is_device_ptr(dst)) {
+    TW_CK(cudaMemcpyAsync(dst, src_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    TW_CK(cudaStreamSynchronize(c->stream));
+  } else {
+    std::memcpy(dst, src_host, bytes);
+  }
+  return TW_OK;
+}
+
+// Copies bytes from device scratch to a host or device pointer.
+int put_from_device(tw_ctx* c, void* dst, const void* src_dev, size_t bytes) {
+  if (bytes == 0 || dst == nullptr) return TW_OK;
+  TW_CK(cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDefault, c->stream));
+  TW_CK(cudaStreamSynchronize(c->stream));
+  return TW_OK;
+}
+
+size_t total_bytes(const tw_ctx* c) { return c->keys.bytes + c->pred.bytes + c->table.bytes; }
+
+// Grows b to at least need bytes, keeping its first keep bytes.  Growth is
+// geometric while the cap allows it.
+int grow(tw_ctx* c, DevBuf* b, size_t need, size_t keep) {
+  if (need <= b->bytes) return TW_OK;
+  const size_t others = total_bytes(c) - b->bytes;
+  if (others + need > c->mem_cap) return TW_ERR_CAPACITY;
+  size_t want = std::max(need, b->bytes * 2);
+  if (others + want > c->mem_cap) want = need;
+  want = (want + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (want == need) return TW_ERR_CAPACITY;
+    want = (need + 255) & ~size_t(255);
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      return TW_ERR_CAPACITY;
+    }
+  }
+  if (keep > 0 && b->ptr) {
+    TW_CK(cudaMemcpyAsync(p, b->ptr, std::min(keep, b->bytes), cudaMemcpyDeviceToDevice, c->stream));
+    TW_CK(cudaStreamSynchronize(c->stream));
+  }
+  if (b->ptr) {
+    TW_CK(cudaStreamSynchronize(c->stream));
+    cudaFree(b->ptr);
+  }
+  b->ptr = p;
+  b->bytes = want;
+  return TW_OK;
+}
+
+// A validated graph in the 64-bit-word row layout of the ABI.
+struct HostGraph {
+  int n = 0;
+  int words = 1;
+  std::vector<uint64_t> rows;  // n * words
+};
+
+int validate(const uint64_t* rows, int n, HostGraph* g) {
+  if (n < 1 || n > TW_MAX_N) return TW_ERR_INVALID;
+  const int W = (n + 63) / 64;
+  g->n = n;
+  g->words = W;
+  g->rows.assign(rows, rows + (size_t)n * W);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < W * 64; ++c) {
+      const bool bit = (g->rows[(size_t)r * W + (c >> 6)] >> (c & 63)) & 1ull;
+      if (!bit) continue;
+      if (c >= n || c == r) return TW_ERR_INVALID;
+      if (!((g->rows[(size_t)c * W + (r >> 6)] >> (r & 63)) & 1ull)) return TW_ERR_INVALID;
+    }
+  return TW_OK;
+}
+
+int load_graph(const uint64_t* adj, int n, HostGraph* g) {
+  if (adj == nullptr || n < 1 || n > TW_MAX_N) return TW_ERR_INVALID;
+  const int W = (n + 63) / 64;
+  std::vector<uint64_t> tmp((size_t)n * W);
+  int rc = fetch(tmp.data(), adj, tmp.size() * sizeof(uint64_t));
+  if (rc) return rc;
+  return validate(tmp.data(), n, g);
+}
+
+// Layout of the small device buffer.
+struct SmallLayout {
+  size_t adj = 0;       // TW_MAX_N keys of 16 bytes
+  size_t adj64 = 2048;  // TW_MAX_N * 2 uint64
+  size_t walk = 4096;   // (TW_MAX_N + 1) keys of 16 bytes
+  size_t order = 8192;  // TW_MAX_N int32
+  size_t parent = 8704; // TW_MAX_N int32
+  size_t bags = 9216;   // TW_MAX_N * 2 uint64
+  size_t bounds = 11264;// 4 int32
+};
+
+char* small_at(tw_ctx* c, size_t off) { return static_cast<char*>(c->small.ptr) + off; }
+
+// Uploads the adjacency in the key layout of class kc and in 64-bit rows.
+int upload_graph(tw_ctx* c, const HostGraph& g, KeyClass kc) {
+  SmallLayout L;
+  std::vector<unsigned char> buf(TW_MAX_N * 16, 0);
+  const size_t w = key_bytes(kc);
+  for (int r = 0; r < g.n; ++r) {
+    const uint64_t lo = g.rows[(size_t)r * g.words];
+    const uint64_t hi = g.words > 1 ? g.rows[(size_t)r * g.words + 1] : 0;
+    if (kc == kKey32) {
+      const uint32_t x = (uint32_t)lo;
+      std::memcpy(&buf[r * w], &x, 4);
+    } else if (kc == kKey64) {
+      std::memcpy(&buf[r * w], &lo, 8);
+    } else {
+      std::memcpy(&buf[r * w], &lo, 8);
+      std::memcpy(&buf[r * w + 8], &hi, 8);
+    }
+  }
+  TW_CK(cudaMemcpyAsync(small_at(c, L.adj), buf.data(), (size_t)g.n * w, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(cudaMemcpyAsync(small_at(c, L.adj64), g.rows.data(), g.rows.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  return TW_OK;
+}
+
+struct LevelRec {
+  unsigned long long off = 0;
+  unsigned long long count = 0;
+};
+
+unsigned long long next_pow2(unsigned long long x) {
+  unsigned long long p = 64;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+double binom(int n, int r) {
+  if (r < 0 || r > n) return 0.0;
+  double b = 1.0;
+  for (int i = 1; i <= r; ++i) b = b * (n - r + i) / i;
+  return b;
+}
+
+struct DecideResult {
+  int yes = 0;
+  std::vector<LevelRec> levels;
+  unsigned long long states_expanded = 0, candidates = 0, feasible = 0, peak_bytes = 0, retries = 0;
+  std::vector<unsigned long long> fp_sum, fp_xor;
+};
+
+// One run of Listing 1 at bound k on the graph already uploaded.
+int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
+  const size_t w = key_bytes(kc);
+  SmallLayout L;
+  R->levels.clear();
+  R->fp_sum.assign(1, 0ull);  // fp of the empty set is 0
+  R->fp_xor.assign(1, 0ull);
+  int rc = grow(c, &c->keys, 64 * w, 0);
+  if (rc) return rc;
+  rc = grow(c, &c->pred, 64, 0);
+  if (rc) return rc;
+  TW_CK(cudaMemsetAsync(c->keys.ptr, 0, w, c->stream));
+  R->levels.push_back({0, 1});
+  R->peak_bytes = w + 1;
+  if (k >= n - 1) {
+    R->yes = 1;
+    return TW_OK;
+  }
+  const int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
+  unsigned long long kept_states = 1;  // states of kept levels (keep mode)
+  for (int i = 0; i <= n - k - 2; ++i) {
+    const LevelRec cur = R->levels[i];
+    double est;
+    if (i == 0) {
+      est = n;
+    } else {
+      const double prev = (double)R->levels[i - 1].count;
+      double r = prev > 0 ? (double)cur.count / prev : 1.0;
+      r = std::min(std::max(r, 0.5), (double)(n - i));
+      est = (double)cur.count * r * 1.5 + 256.0;
+      est = std::min(est, (double)cur.count * (double)(n - i) + 1.0);
+      est = std::min(est, binom(n, i + 1) + 1.0);
+    }
+    unsigned long long out_cap = (unsigned long long)std::ceil(est);
+    unsigned long long slots = next_pow2((unsigned long long)std::ceil(est * 100.0 / load_pct));
+    LevelRec nxt;
+    for (int attempt = 0;; ++attempt) {
+      if (attempt > 40) return TW_ERR_CAPACITY;
+      unsigned long long off;
+      if (keep_levels) {
+        off = cur.off + cur.count;
+      } else {
+        off = (out_cap <= cur.off) ? 0ull : cur.off + cur.count;
+      }
+      const unsigned long long live_end = cur.off + cur.count;  // data to keep on growth
+      rc = grow(c, &c->table, slots * w, 0);
+      if (rc) return rc;
+      rc = grow(c, &c->keys, (size_t)(off + out_cap) * w, (size_t)live_end * w);
+      if (rc) return rc;
+      rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)live_end);
+      if (rc) return rc;
+      TW_CK(launch_clear(c->table.ptr, slots * w, c->d_ctr, c->stream));
+      ExpandLaunch a;
+      a.kc = kc;
+      a.in_keys = static_cast<char*>(c->keys.ptr) + cur.off * w;
+      a.n_in = cur.count;
+      a.adj = small_at(c, L.adj);
+      a.n = n;
+      a.k = k;
+      a.table = c->table.ptr;
+      a.table_slots = slots;
+      a.max_probes = max_probes;
+      a.out_keys = static_cast<char*>(c->keys.ptr) + off * w;
+      a.out_pred = static_cast<uint8_t*>(c->pred.ptr) + off;
+      a.out_cap = out_cap;
+      a.ctr = c->d_ctr;
+      a.block_threads = c->cfg.block_threads;
+      a.grid = 0;
+      TW_CK(launch_expand(a, c->stream));
+      TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      const LevelCounters h = *c->h_ctr;
+      const bool table_full = (h.overflow & 2u) || h.out_count * 100ull > slots * 90ull;
+      if (table_full) {
+        const double grown = std::max((double)out_cap * 2.0, (double)h.out_count * 1.5);
+        out_cap = (unsigned long long)grown;
+        slots = next_pow2((unsigned long long)std::ceil(grown * 100.0 / load_pct));
+        ++R->retries;
+        continue;
+      }
+      if (h.overflow & 1u) {
+        out_cap = h.out_count;  // exact: every insert that won was counted
+        slots = std::max(slots, next_pow2((unsigned long long)std::ceil((double)out_cap * 100.0 / load_pct)));
+        ++R->retries;
+        continue;
+      }
+      nxt.off = off;
+      nxt.count = h.out_count;
+      R->feasible += h.feasible;
+      const unsigned long long live_states = keep_levels ? kept_states + nxt.count : cur.count + nxt.count;
+      R->peak_bytes = std::max<unsigned long long>(R->peak_bytes, live_states * (w + 1) + slots * w);
+      break;
+    }
+    R->states_expanded += cur.count;
+    R->candidates += cur.count * (unsigned long long)(n - i);
+    if (keep_levels) kept_states += nxt.count;
+    R->levels.push_back(nxt);
+    if (c->cfg.fingerprints) {
+      TW_CK(launch_fingerprint(kc, static_cast<char*>(c->keys.ptr) + nxt.off * w, nxt.count, c->d_ctr, c->stream));
+      TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      R->fp_sum.push_back(c->h_ctr->fp_sum);
+      R->fp_xor.push_back(c->h_ctr->fp_xor);
+    }
+    if (nxt.count == 0) break;
+  }
+  const int last = (int)R->levels.size() - 1;
+  R->yes = (last == n - k - 1 && R->levels[last].count > 0) ? 1 : 0;
+  return TW_OK;
+}
+
+// Backward walk through the kept levels into the device order buffer.
+int reconstruct(tw_ctx* c, KeyClass kc, int n, const DecideResult& R) {
+  SmallLayout L;
+  const size_t w = key_bytes(kc);
+  const int last = (int)R.levels.size() - 1;
+  int32_t* d_order = reinterpret_cast<int32_t*>(small_at(c, L.order));
+  void* walk = small_at(c, L.walk);
+  char* keys = static_cast<char*>(c->keys.ptr);
+  const uint8_t* pred = static_cast<const uint8_t*>(c->pred.ptr);
+  TW_CK(launch_walk_init(kc, keys + R.levels[last].off * w, walk, last, c->stream));
+  for (int j = last; j >= 1; --j) {
+    const LevelRec& lr = R.levels[j];
+    TW_CK(launch_walk_step(kc, keys + lr.off * w, pred + lr.off, lr.count, walk, j, d_order, c->stream));
+  }
+  TW_CK(launch_walk_finish(kc, walk, last, n, d_order, c->stream));
+  return TW_OK;
+}
+
+void fill_stats(const DecideResult& R, int k, tw_stats* st, bool reset_totals) {
+  if (!st) return;
+  if (reset_totals) {
+    st->states_expanded = st->candidates = st->feasible = st->peak_frontier_bytes = 0;
+    st->decide_runs = st->level_retries = 0;
+  }
+  st->levels = (int)R.levels.size();
+  st->k = k;
+  for (int i = 0; i <= TW_MAX_N; ++i) {
+    const bool in = i < (int)R.levels.size();
+    st->level_size[i] = in ? R.levels[i].count : 0;
+    st->level_fp_sum[i] = (in && i < (int)R.fp_sum.size()) ? R.fp_sum[i] : 0;
+    st->level_fp_xor[i] = (in && i < (int)R.fp_xor.size()) ? R.fp_xor[i] : 0;
+  }
+  st->states_expanded += R.states_expanded;
+  st->candidates += R.candidates;
+  st->feasible += R.feasible;
+  st->peak_frontier_bytes = std::max<uint64_t>(st->peak_frontier_bytes, R.peak_bytes);
+  st->decide_runs += 1;
+  st->level_retries += R.retries;
+}
+
+int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order, tw_stats* st) {
+  Timer t;
+  if (k < 0 || yes == nullptr) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  const KeyClass kc = key_class_for(g.n);
+  int rc = upload_graph(c, g, kc);
+  if (rc) return rc;
+  DecideResult R;
+  rc = run_decide(c, kc, g.n, k, order != nullptr, &R);
+  if (rc) return rc;
+  if (R.yes && order) {
+    rc = reconstruct(c, kc, g.n, R);
+    if (rc) return rc;
+    rc = put_from_device(c, order, small_at(c, SmallLayout().order), (size_t)g.n * 4);
+    if (rc) return rc;
+  }
+  TW_CK(cudaStreamSynchronize(c->stream));
+  fill_stats(R, k, st, true);
+  int y = R.yes;
+  rc = put(c, yes, &y, sizeof(int));
+  if (rc) return rc;
+  if (st) st->seconds = t.seconds();
+  return TW_OK;
+}
+
+int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]) {
+  SmallLayout L;
+  int32_t* d_out = reinterpret_cast<int32_t*>(small_at(c, L.bounds));
+  int32_t* d_n = d_out + 4;
+  int64_t* d_off = reinterpret_cast<int64_t*>(small_at(c, L.bounds + 64));
+  const int32_t nn = g.n;
+  const int64_t off = 0;
+  TW_CK(cudaMemcpyAsync(d_n, &nn, 4, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(cudaMemcpyAsync(d_off, &off, 8, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(launch_bounds(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), d_n, d_off, 1, d_out,
+                      nullptr, c->stream));
+  TW_CK(cudaMemcpyAsync(out, d_out, 16, cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaStreamSynchronize(c->stream));
+  return TW_OK;
+}
+
+int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int32_t* td_parent, uint64_t* td_bags,
+                tw_stats* st, int k_first) {
+  Timer t;
+  TW_CK(cudaSetDevice(c->device));
+  const KeyClass kc = key_class_for(g.n);
+  int rc = upload_graph(c, g, kc);
+  if (rc) return rc;
+  int32_t b[4];
+  rc = bounds_graph(c, g, b);
+  if (rc) return rc;
+  const int lb = std::max(b[0], b[1]);
+  const int ub = std::min(b[2], b[3]);
+  const bool want_walk = order || td_parent || td_bags;
+  if (st) {
+    st->states_expanded = st->candidates = st->feasible = st->peak_frontier_bytes = 0;
+    st->decide_runs = st->level_retries = 0;
+  }
+  int tw = -1;
+  DecideResult R;
+  int k0 = std::max(lb, k_first);
+  if (c->cfg.ub_shortcut && lb == ub && !want_walk) {
+    tw = ub;
+  } else {
+    for (int k = k0; k < g.n; ++k) {
+      rc = run_decide(c, kc, g.n, k, want_walk, &R);
+      if (rc) return rc;
+      fill_stats(R, k, st, false);
+      if (R.yes) {
+        tw = k;
+        break;
+      }
+    }
+  }
+  if (tw < 0) return TW_ERR_CUDA;
+  if (want_walk && R.yes) {
+    SmallLayout L;
+    rc = reconstruct(c, kc, g.n, R);
+    if (rc) return rc;
+    int32_t* d_order = reinterpret_cast<int32_t*>(small_at(c, L.order));
+    if (td_parent || td_bags) {
+      TW_CK(launch_td(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), g.n, g.words, d_order,
+                      reinterpret_cast<int32_t*>(small_at(c, L.parent)),
+                      reinterpret_cast<unsigned long long*>(small_at(c, L.bags)), c->stream));
+    }
+    rc = put_from_device(c, order, d_order, (size_t)g.n * 4);
+    if (rc) return rc;
+    rc = put_from_device(c, td_parent, small_at(c, L.parent), (size_t)g.n * 4);
+    if (rc) return rc;
+    rc = put_from_device(c, td_bags, small_at(c, L.bags), (size_t)g.n * g.words * 8);
+    if (rc) return rc;
+  }
+  TW_CK(cudaStreamSynchronize(c->stream));
+  rc = put(c, tw_out, &tw, sizeof(int));
+  if (rc) return rc;
+  if (st) st->seconds = t.seconds();
+  return TW_OK;
+}
+
+
+// Scratch staging: a bump allocator over ctx->scratch (256-byte aligned
+// pieces).  reserve() must be called with the total before any piece is taken.
+struct Stager {
+  tw_ctx* c;
+  size_t used = 0;
+  explicit Stager(tw_ctx* cc) : c(cc) {}
+  int reserve(size_t total) {
+    if (total > c->scratch.bytes) {
+      if (c->scratch.ptr) {
+        TW_CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->scratch.ptr);
+        c->scratch.ptr = nullptr;
+        c->scratch.bytes = 0;
+      }
+      const size_t want = (total + 4095) & ~size_t(4095);
+      if (cudaMalloc(&c->scratch.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        return TW_ERR_CAPACITY;
+      }
+      c->scratch.bytes = want;
+    }
+    return TW_OK;
+  }
+  void* take(size_t bytes) {
+    char* p = static_cast<char*>(c->scratch.ptr) + used;
+    used += (bytes + 255) & ~size_t(255);
+    return p;
+  }
+  // Device copy of a host or device array (device arrays are used in place).
+  int in(const void* src, size_t bytes, const void** out) {
+    if (is_device_ptr(src)) {
+      *out = src;
+      take(bytes);
+      return TW_OK;
+    }
+    void* d = take(bytes);
+    TW_CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    *out = d;
+    return TW_OK;
+  }
+};
+
+
+// Decide runs of one graph guided by a proposed bound: decide(k0) and
+// decide(k0-1) first, then walk up (on no) or down (on yes) until yes at tw
+// and no at tw-1 (or tw = lower bound) certify the answer.  Returns the
+// treewidth in *tw_out and the ordering of the yes run at tw in order_host.
+int solve_hinted(tw_ctx* c, const HostGraph& g, float hint, int* tw_out, std::vector<int32_t>* order_host,
+                 tw_stats* st) {
+  const KeyClass kc = key_class_for(g.n);
+  int rc = upload_graph(c, g, kc);
+  if (rc) return rc;
+  int32_t b[4];
+  if ((rc = bounds_graph(c, g, b))) return rc;
+  const int lb = std::max(b[0], b[1]);
+  int k0 = (int)std::lround(hint);
+  k0 = std::min(std::max(k0, lb), g.n - 1);
+  DecideResult R;
+  SmallLayout L;
+  auto run = [&](int k, int* yes) -> int {
+    int r = run_decide(c, kc, g.n, k, order_host != nullptr, &R);
+    if (r) return r;
+    fill_stats(R, k, st, false);
+    *yes = R.yes;
+    if (R.yes && order_host) {
+      if ((r = reconstruct(c, kc, g.n, R))) return r;
+      order_host->resize(g.n);
+      TW_CK(cudaMemcpyAsync(order_host->data(), small_at(c, L.order), (size_t)g.n * 4, cudaMemcpyDeviceToHost,
+                            c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+    }
+    return TW_OK;
+  };
+  int yes = 0;
+  if ((rc = run(k0, &yes))) return rc;
+  if (yes) {
+    int k = k0;
+    while (k > lb) {
+      int y2 = 0;
+      if ((rc = run(k - 1, &y2))) return rc;
+      if (!y2) break;
+      --k;
+    }
+    *tw_out = k;
+  } else {
+    int k = k0 + 1;
+    for (;; ++k) {
+      int y2 = 0;
+      if ((rc = run(k, &y2))) return rc;
+      if (y2) break;
+    }
+    *tw_out = k;
+  }
+  return TW_OK;
+}
+
+int solve_batch_loop(tw_ctx* c, const std::vector<uint64_t>& hadj, const std::vector<int32_t>& hn,
+                     const std::vector<int64_t>& hoff, int* tw, int32_t* orders, int* status,
+                     const std::vector<float>* hint, tw_stats* st, const Timer& t) {
+  const int G = (int)hn.size();
+  std::vector<int> htw(G, -1), hst(G, TW_OK);
+  int64_t total_n = 0;
+  for (int g = 0; g < G; ++g) total_n += hn[g];
+  std::vector<int32_t> hord(orders ? (size_t)total_n : 0, -1);
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+  }
+  int worst = TW_OK;
+  int64_t pos = 0;
+  for (int g = 0; g < G; ++g) {
+    HostGraph hg;
+    int rc = validate(hadj.data() + hoff[g], hn[g], &hg);
+    if (rc == TW_OK) {
+      std::vector<int32_t> ord;
+      if (hint) {
+        rc = solve_hinted(c, hg, (*hint)[g], &htw[g], orders ? &ord : nullptr, st);
+      } else {
+        tw_stats local;
+        std::memset(&local, 0, sizeof(local));
+        ord.assign(hg.n, -1);
+        rc = solve_graph(c, hg, &htw[g], orders ? ord.data() : nullptr, nullptr, nullptr, &local, 0);
+        if (st && rc == TW_OK) {
+          st->states_expanded += local.states_expanded;
+          st->candidates += local.candidates;
+          st->feasible += local.feasible;
+          st->peak_frontier_bytes = std::max(st->peak_frontier_bytes, local.peak_frontier_bytes);
+          st->decide_runs += local.decide_runs;
+          st->level_retries += local.level_retries;
+        }
+      }
+      if (rc == TW_OK && orders)
+        for (int j = 0; j < hg.n; ++j) hord[pos + j] = ord[j];
+    }
+    if (rc != TW_OK) htw[g] = -1;
+    hst[g] = rc;
+    worst = std::max(worst, rc);
+    pos += hn[g];
+  }
+  int rc = put(c, tw, htw.data(), (size_t)G * sizeof(int));
+  if (rc) return rc;
+  if ((rc = put(c, status, hst.data(), (size_t)G * sizeof(int)))) return rc;
+  if (orders && (rc = put(c, orders, hord.data(), hord.size() * 4))) return rc;
+  if (st) st->seconds = t.seconds();
+  return worst;
+}
+
+size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Batched per-graph validation into 64-bit rows.
+int load_batch(const uint64_t* adj_concat, const int32_t* n, const int64_t* row_offset, int num_graphs,
+               std::vector<int32_t>* hn, std::vector<int64_t>* hoff, std::vector<uint64_t>* hadj) {
+  if (!adj_concat || !n || !row_offset || num_graphs < 0) return TW_ERR_INVALID;
+  hn->resize(num_graphs);
+  hoff->resize(num_graphs);
+  int rc = fetch(hn->data(), n, (size_t)num_graphs * 4);
+  if (rc) return rc;
+  rc = fetch(hoff->data(), row_offset, (size_t)num_graphs * 8);
+  if (rc) return rc;
+  int64_t words = 0;
+  for (int g = 0; g < num_graphs; ++g) {
+    const int ng = (*hn)[g];
+    if (ng < 1 || ng > TW_MAX_N || (*hoff)[g] < 0) return TW_ERR_INVALID;
+    words = std::max<int64_t>(words, (*hoff)[g] + (int64_t)ng * ((ng + 63) / 64));
+  }
+  hadj->resize((size_t)words);
+  return fetch(hadj->data(), adj_concat, (size_t)words * 8);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tw_abi_version(void) { return TW_ABI_VERSION; }
+
+const char* tw_strerror(int status) {
+  switch (status) {
+    case TW_OK: return "ok";
+    case TW_ERR_INVALID: return "invalid argument (graph, n, k or a required pointer)";
+    case TW_ERR_CAPACITY: return "frontier or table would exceed the memory cap; no answer given";
+    case TW_ERR_TIMEOUT: return "a bounded device wait expired";
+    case TW_ERR_CUDA: return "a CUDA runtime call failed";
+    default: return "unknown status";
+  }
+}
+
+int tw_create(tw_ctx** out, const tw_config* cfg) {
+  if (out == nullptr) return TW_ERR_INVALID;
+  *out = nullptr;
+  tw_config cf{};
+  if (cfg) cf = *cfg;
+  for (int r : cf.reserved)
+    if (r != 0) return TW_ERR_INVALID;
+  if (cf.block_threads != 0 && cf.block_threads != 64 && cf.block_threads != 128 && cf.block_threads != 256)
+    return TW_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cf.device < 0 || cf.device >= ndev) {
+    cudaGetLastError();
+    return TW_ERR_CUDA;
+  }
+  tw_ctx* c = new tw_ctx();
+  c->device = cf.device;
+  c->cfg = cf;
+  auto fail = [&](int code) {
+    tw_destroy(c);
+    return code;
+  };
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(TW_ERR_CUDA);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(TW_ERR_CUDA);
+  const size_t dflt = std::min<size_t>(150ull << 30, (size_t)(0.9 * (double)free_b));
+  c->mem_cap = cf.mem_cap_bytes ? cf.mem_cap_bytes : dflt;
+  if (cf.stream) {
+    c->stream = static_cast<cudaStream_t>(cf.stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(TW_ERR_CUDA);
+    c->own_stream = true;
+  }
+  if (cudaMalloc(&c->small.ptr, kSmallBytes) != cudaSuccess) return fail(TW_ERR_CUDA);
+  c->small.bytes = kSmallBytes;
+  if (cudaMalloc(reinterpret_cast<void**>(&c->d_ctr), sizeof(LevelCounters)) != cudaSuccess) return fail(TW_ERR_CUDA);
+  if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_ctr), sizeof(LevelCounters), cudaHostAllocDefault) != cudaSuccess)
+    return fail(TW_ERR_CUDA);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  *out = c;
+  return TW_OK;
+}
+
+void tw_destroy(tw_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (DevBuf* b : {&c->keys, &c->pred, &c->table, &c->small, &c->scratch})
+    if (b->ptr) cudaFree(b->ptr);
+  if (c->d_ctr) cudaFree(c->d_ctr);
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  cudaGetLastError();
+  delete c;
+}
+
+int tw_decide(tw_ctx* c, const uint64_t* adj, int n, int k, int* yes, int32_t* order, tw_stats* st) {
+  if (!c || !yes || k < 0) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  HostGraph g;
+  int rc = load_graph(adj, n, &g);
+  if (rc) return rc;
+  return decide_graph(c, g, k, yes, order, st);
+}
+
+int tw_decide_u32(tw_ctx* c, const uint32_t* adj_rows, int n, int k, int* yes, int32_t* order, tw_stats* st) {
+  if (!c || !yes || !adj_rows || k < 0 || n < 1 || n > 32) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  std::vector<uint32_t> r32(n);
+  int rc = fetch(r32.data(), adj_rows, (size_t)n * 4);
+  if (rc) return rc;
+  std::vector<uint64_t> r64(r32.begin(), r32.end());
+  HostGraph g;
+  rc = validate(r64.data(), n, &g);
+  if (rc) return rc;
+  return decide_graph(c, g, k, yes, order, st);
+}
+
+int tw_solve(tw_ctx* c, const uint64_t* adj, int n, int* tw, int32_t* order, int32_t* td_parent, uint64_t* td_bags,
+             tw_stats* st) {
+  if (!c || !tw) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  HostGraph g;
+  int rc = load_graph(adj, n, &g);
+  if (rc) return rc;
+  return solve_graph(c, g, tw, order, td_parent, td_bags, st, 0);
+}
+
+int tw_bounds(tw_ctx* c, const uint64_t* adj, int n, int32_t out[4]) {
+  if (!c || !out) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  HostGraph g;
+  int rc = load_graph(adj, n, &g);
+  if (rc) return rc;
+  rc = upload_graph(c, g, key_class_for(g.n));
+  if (rc) return rc;
+  int32_t b[4];
+  rc = bounds_graph(c, g, b);
+  if (rc) return rc;
+  return put(c, out, b, sizeof(b));
+}
+
+int tw_features_batch(tw_ctx* c, const uint64_t* adj_concat, const int32_t* n, const int64_t* row_offset,
+                      int num_graphs, float* feats) {
+  if (!c || !feats || num_graphs < 0) return TW_ERR_INVALID;
+  if (num_graphs == 0) return TW_OK;
+  TW_CK(cudaSetDevice(c->device));
+  std::vector<int32_t> hn;
+  std::vector<int64_t> hoff;
+  std::vector<uint64_t> hadj;
+  int rc = load_batch(adj_concat, n, row_offset, num_graphs, &hn, &hoff, &hadj);
+  if (rc) return rc;
+  for (int g = 0; g < num_graphs; ++g) {
+    HostGraph tmp;
+    rc = validate(hadj.data() + hoff[g], hn[g], &tmp);
+    if (rc) return rc;
+  }
+  Stager S(c);
+  const size_t fb = (size_t)num_graphs * 12 * 4;
+  rc = S.reserve(pad256(hadj.size() * 8) + pad256(hn.size() * 4) + pad256(hoff.size() * 8) + pad256(fb) + 1024);
+  if (rc) return rc;
+  const void *d_adj, *d_n, *d_off;
+  if ((rc = S.in(hadj.data(), hadj.size() * 8, &d_adj))) return rc;
+  if ((rc = S.in(hn.data(), hn.size() * 4, &d_n))) return rc;
+  if ((rc = S.in(hoff.data(), hoff.size() * 8, &d_off))) return rc;
+  float* d_f = static_cast<float*>(S.take(fb));
+  TW_CK(launch_bounds(static_cast<const unsigned long long*>(d_adj), static_cast<const int32_t*>(d_n),
+                      static_cast<const int64_t*>(d_off), num_graphs, nullptr, d_f, c->stream));
+  return put_from_device(c, feats, d_f, fb);
+}
+
+static const int kMlpParams = 32 * 12 + 32 + 32 + 1;
+
+int tw_mlp_forward(tw_ctx* c, const float* params, const float* x, int batch, float* yhat) {
+  if (!c || !params || !x || !yhat || batch < 0) return TW_ERR_INVALID;
+  if (batch == 0) return TW_OK;
+  TW_CK(cudaSetDevice(c->device));
+  Stager S(c);
+  int rc = S.reserve(pad256(kMlpParams * 4) + pad256((size_t)batch * 48) + pad256((size_t)batch * 4) + 1024);
+  if (rc) return rc;
+  const void *dp, *dx;
+  if ((rc = S.in(params, kMlpParams * 4, &dp))) return rc;
+  if ((rc = S.in(x, (size_t)batch * 48, &dx))) return rc;
+  float* dy = static_cast<float*>(S.take((size_t)batch * 4));
+  TW_CK(launch_mlp_forward(static_cast<const float*>(dp), static_cast<const float*>(dx), batch, dy, c->stream));
+  return put_from_device(c, yhat, dy, (size_t)batch * 4);
+}
+
+int tw_mlp_grad(tw_ctx* c, const float* params, const float* x, const float* y, int batch, float* grad) {
+  if (!c || !params || !x || !y || !grad || batch <= 0) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  const int blocks = std::max(1, std::min(c->sms * 2, (batch + 127) / 128));
+  Stager S(c);
+  int rc = S.reserve(pad256(kMlpParams * 4) * 2 + pad256((size_t)batch * 48) + pad256((size_t)batch * 4) +
+                     pad256((size_t)blocks * kMlpParams * 4) + 1024);
+  if (rc) return rc;
+  const void *dp, *dx, *dyv;
+  if ((rc = S.in(params, kMlpParams * 4, &dp))) return rc;
+  if ((rc = S.in(x, (size_t)batch * 48, &dx))) return rc;
+  if ((rc = S.in(y, (size_t)batch * 4, &dyv))) return rc;
+  float* dg = static_cast<float*>(S.take(kMlpParams * 4));
+  float* part = static_cast<float*>(S.take((size_t)blocks * kMlpParams * 4));
+  TW_CK(launch_mlp_grad(static_cast<const float*>(dp), static_cast<const float*>(dx), static_cast<const float*>(dyv),
+                        batch, dg, part, blocks, c->stream));
+  return put_from_device(c, grad, dg, kMlpParams * 4);
+}
+
+int tw_mlp_adam(tw_ctx* c, float* params, const float* grad, float* m, float* v, int t, float lr, float beta1,
+                float beta2, float eps) {
+  if (!c || !params || !grad || !m || !v || t < 1) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  Stager S(c);
+  int rc = S.reserve(pad256(kMlpParams * 4) * 4 + 1024);
+  if (rc) return rc;
+  const void *dp, *dg, *dm, *dv;
+  if ((rc = S.in(params, kMlpParams * 4, &dp))) return rc;
+  if ((rc = S.in(grad, kMlpParams * 4, &dg))) return rc;
+  if ((rc = S.in(m, kMlpParams * 4, &dm))) return rc;
+  if ((rc = S.in(v, kMlpParams * 4, &dv))) return rc;
+  TW_CK(launch_mlp_adam(const_cast<float*>(static_cast<const float*>(dp)), static_cast<const float*>(dg),
+                        const_cast<float*>(static_cast<const float*>(dm)), const_cast<float*>(static_cast<const float*>(dv)),
+                        t, lr, beta1, beta2, eps, c->stream));
+  if (dp != params && (rc = put_from_device(c, params, dp, kMlpParams * 4))) return rc;
+  if (dm != m && (rc = put_from_device(c, m, dm, kMlpParams * 4))) return rc;
+  if (dv != v && (rc = put_from_device(c, v, dv, kMlpParams * 4))) return rc;
+  TW_CK(cudaStreamSynchronize(c->stream));
+  return TW_OK;
+}
+
+int tw_mlp_train(tw_ctx* c, float* params, const float* x, const float* y, int batch_total, int minibatch, int epochs,
+                 const int32_t* perm, float lr, float* loss_out) {
+  if (!c || !params || !x || !y || !perm || batch_total <= 0 || minibatch <= 0 || epochs <= 0) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  const size_t pb = (size_t)epochs * batch_total * 4;
+  {
+    std::vector<int32_t> hp((size_t)epochs * batch_total);
+    int r = fetch(hp.data(), perm, pb);
+    if (r) return r;
+    for (int32_t i : hp)
+      if (i < 0 || i >= batch_total) return TW_ERR_INVALID;
+  }
+  Stager S(c);
+  int rc = S.reserve(pad256(kMlpParams * 4) * 3 + pad256((size_t)batch_total * 48) + pad256((size_t)batch_total * 4) +
+                     pad256(pb) + pad256((size_t)epochs * 4) + 2048);
+  if (rc) return rc;
+  const void *dp, *dx, *dy, *dperm;
+  if ((rc = S.in(params, kMlpParams * 4, &dp))) return rc;
+  if ((rc = S.in(x, (size_t)batch_total * 48, &dx))) return rc;
+  if ((rc = S.in(y, (size_t)batch_total * 4, &dy))) return rc;
+  if ((rc = S.in(perm, pb, &dperm))) return rc;
+  float* dm = static_cast<float*>(S.take(kMlpParams * 4));
+  float* dv = static_cast<float*>(S.take(kMlpParams * 4));
+  float* dl = static_cast<float*>(S.take((size_t)epochs * 4));
+  TW_CK(cudaMemsetAsync(dm, 0, kMlpParams * 4, c->stream));
+  TW_CK(cudaMemsetAsync(dv, 0, kMlpParams * 4, c->stream));
+  TW_CK(launch_mlp_train(const_cast<float*>(static_cast<const float*>(dp)), dm, dv, static_cast<const float*>(dx),
+                         static_cast<const float*>(dy), batch_total, minibatch, epochs,
+                         static_cast<const int32_t*>(dperm), lr, dl, c->stream));
+  if (dp != params && (rc = put_from_device(c, params, dp, kMlpParams * 4))) return rc;
+  if (loss_out && (rc = put_from_device(c, loss_out, dl, (size_t)epochs * 4))) return rc;
+  TW_CK(cudaStreamSynchronize(c->stream));
+  return TW_OK;
+}
+
+int tw_solve_batch(tw_ctx* c, const uint64_t* adj_concat, const int32_t* n, const int64_t* row_offset,
+                   int num_graphs, int* tw, int32_t* orders, int* status, const float* k_hint, tw_stats* st) {
+  if (!c || !tw || !status || num_graphs < 0) return TW_ERR_INVALID;
+  Timer t;
+  TW_CK(cudaSetDevice(c->device));
+  std::vector<int32_t> hn;
+  std::vector<int64_t> hoff;
+  std::vector<uint64_t> hadj;
+  int rc = load_batch(adj_concat, n, row_offset, num_graphs, &hn, &hoff, &hadj);
+  if (rc) return rc;
+  std::vector<float> hint;
+  if (k_hint) {
+    hint.resize(num_graphs);
+    if ((rc = fetch(hint.data(), k_hint, (size_t)num_graphs * 4))) return rc;
+  }
+  return solve_batch_loop(c, hadj, hn, hoff, tw, orders, status, k_hint ? &hint : nullptr, st, t);
+}
+
+}  // extern "C"

@@ -1,0 +1,470 @@
+// Wavefront expansion, duplicate removal, and ordering reconstruction.
+//
+// One level of Listing 1 (van der Zanden & Bodlaender, arXiv 1709.09990,
+// Section 3.1): every set S of L_i is extended by every vertex v outside S
+// whose degree after eliminating S, |Q(S, v)|, is at most k.  The extensions
+// S u {v} are deduplicated (Section 3.2) in an exact open-addressing hash
+// table and appended to L_{i+1} together with the predecessor vertex v.
+//
+// GB300 mapping.  A warp takes 32 consecutive states (coalesced key loads).
+//  1. Thread-per-state: the components of G[S] are found by a bitset flood
+//     fill over the adjacency rows held in shared memory; |S| row reads in
+//     total.  Each component C contributes its outer boundary B_C = N(C) \ S.
+//     Then Q(S, v) = (N(v) u U{B_C : v in B_C}) \ (S u {v}), the bitset form
+//     of the depth-first search of Listing 1 (lines 7-19): a vertex outside S
+//     is reached from v through S exactly when it borders a component of G[S]
+//     that v borders.  Components with |B_C| >= k+2 make every v in B_C
+//     infeasible at once; up to 8 other boundaries stay in registers, and a
+//     state with more falls back to a flood fill per candidate v.
+//  2. Warp-cooperative insert: the feasible (S, v) pairs of the 32 states are
+//     packed into a per-warp shared-memory queue, and the whole warp inserts
+//     32 of them at a time with one 4/8/16-byte compare-and-swap each, so
+//     lanes do not idle on states with few extensions.
+//  3. The winners of a round append (S u {v}, v) to L_{i+1} with one atomic
+//     add per warp.
+#include <cuda_runtime.h>
+
+#include "tw_internal.h"
+#include "tw_keys.cuh"
+
+namespace tw {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxComps = 8;
+
+template <class K>
+struct ExpandParams {
+  const K* in_keys;
+  unsigned long long n_in;
+  const K* adj;
+  int n;
+  int k;
+  K* table;
+  unsigned long long table_mask;
+  int max_probes;
+  K* out_keys;
+  uint8_t* out_pred;
+  unsigned long long out_cap;
+  LevelCounters* ctr;
+};
+
+// The set of vertices v outside S with |Q(S, v)| <= k.
+template <class K>
+__device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict__ sAdj, const K valid,
+                                                 const int k) {
+  K comp_b[kMaxComps];
+#pragma unroll
+  for (int c = 0; c < kMaxComps; ++c) comp_b[c] = kzero<K>();
+  int nc = 0;
+  bool many = false;
+  K dead = kzero<K>();
+  K rem = S;
+  while (!kempty(rem)) {
+    K comp = kzero<K>();
+    K todo = kbit<K>(klowest(rem));
+    K bnd = kzero<K>();
+    while (!kempty(todo)) {
+      const int u = klowest(todo);
+      todo = kdrop_lowest(todo);
+      comp |= kbit<K>(u);
+      const K r = sAdj[u];
+      bnd |= r;
+      todo |= r & rem & ~comp;
+    }
+    rem &= ~comp;
+    bnd &= ~S;
+    const int bs = kpopc(bnd);
+    if (bs >= k + 2) {
+      dead |= bnd;
+    } else if (bs > 0) {
+      if (nc < kMaxComps) {
+#pragma unroll
+        for (int c = 0; c < kMaxComps; ++c)
+          if (c == nc) comp_b[c] = bnd;
+        ++nc;
+      } else {
+        many = true;
+      }
+    }
+  }
+  K cand = valid & ~S & ~dead;
+  K feas = kzero<K>();
+  while (!kempty(cand)) {
+    const int v = klowest(cand);
+    cand = kdrop_lowest(cand);
+    const K nv = sAdj[v];
+    K q = nv & ~S;
+    if (kpopc(q) > k) continue;
+    if (!many) {
+#pragma unroll
+      for (int c = 0; c < kMaxComps; ++c)
+        if (ktest(comp_b[c], v)) q |= comp_b[c];
+    } else {
+      K vis = nv & S;
+      K front = vis;
+      while (!kempty(front)) {
+        const int u = klowest(front);
+        front = kdrop_lowest(front);
+        const K r = sAdj[u];
+        q |= r & ~S;
+        const K nw = r & S & ~vis;
+        vis |= nw;
+        front |= nw;
+      }
+    }
+    q &= ~kbit<K>(v);
+    if (kpopc(q) <= k) feas |= kbit<K>(v);
+  }
+  return feas;
+}
+
+template <class K, int kWarps>
+__global__ void __launch_bounds__(kWarps * 32) expand_insert_kernel(const ExpandParams<K> p) {
+  constexpr int kBits = KeyTraits<K>::kBits;
+  __shared__ K sAdj[kBits];
+  __shared__ K sState[kWarps][32];
+  __shared__ uint16_t sQueue[kWarps][32 * kBits];
+
+  for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const unsigned lanemask_lt = (1u << lane) - 1u;
+  const K valid = kfirst_n<K>(p.n);
+  const K empty = kones<K>();
+  unsigned long long feasible_total = 0;
+  const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
+  const unsigned long long stride = (unsigned long long)gridDim.x * kWarps;
+
+  for (unsigned long long chunk = (unsigned long long)blockIdx.x * kWarps + warp; chunk < n_chunks;
+       chunk += stride) {
+    const unsigned long long idx = chunk * 32ull + lane;
+    const bool active = idx < p.n_in;
+    const K S = active ? p.in_keys[idx] : valid;
+    K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.k) : kzero<K>();
+
+    const int cnt = kpopc(feas);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    int pos = incl - cnt;
+    sState[warp][lane] = S;
+    while (!kempty(feas)) {
+      const int v = klowest(feas);
+      feas = kdrop_lowest(feas);
+      sQueue[warp][pos++] = (uint16_t)((lane << 8) | v);
+    }
+    __syncwarp();
+    feasible_total += (unsigned long long)total;
+
+    for (int base = 0; base < total; base += 32) {
+      const int j = base + lane;
+      bool won = false;
+      K key = kzero<K>();
+      int v = 0;
+      if (j < total) {
+        const uint16_t e = sQueue[warp][j];
+        v = e & 0xff;
+        key = sState[warp][e >> 8] | kbit<K>(v);
+        unsigned long long h = khash(key) & p.table_mask;
+        for (int probe = 0;; ++probe) {
+          const K old = kcas(&p.table[h], empty, key);
+          if (old == empty) {
+            won = true;
+            break;
+          }
+          if (old == key) break;
+          if (probe + 1 >= p.max_probes) {
+            atomicOr(&p.ctr->overflow, 2u);
+            break;
+          }
+          h = (h + 1ull) & p.table_mask;
+        }
+      }
+      const unsigned wmask = __ballot_sync(kFull, won);
+      if (wmask) {
+        const int leader = __ffs(wmask) - 1;
+        unsigned long long b = 0;
+        if (lane == leader) b = atomicAdd(&p.ctr->out_count, (unsigned long long)__popc(wmask));
+        b = __shfl_sync(kFull, b, leader);
+        if (won) {
+          const unsigned long long o = b + (unsigned long long)__popc(wmask & lanemask_lt);
+          if (o < p.out_cap) {
+            p.out_keys[o] = key;
+            p.out_pred[o] = (uint8_t)v;
+          } else {
+            atomicOr(&p.ctr->overflow, 1u);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && feasible_total) atomicAdd(&p.ctr->feasible, feasible_total);
+}
+
+template <class K, int kWarps>
+cudaError_t launch_expand_t(const ExpandLaunch& a, cudaStream_t s) {
+  ExpandParams<K> p;
+  p.in_keys = static_cast<const K*>(a.in_keys);
+  p.n_in = a.n_in;
+  p.adj = static_cast<const K*>(a.adj);
+  p.n = a.n;
+  p.k = a.k;
+  p.table = static_cast<K*>(a.table);
+  p.table_mask = a.table_slots - 1ull;
+  p.max_probes = a.max_probes;
+  p.out_keys = static_cast<K*>(a.out_keys);
+  p.out_pred = a.out_pred;
+  p.out_cap = a.out_cap;
+  p.ctr = a.ctr;
+  if (a.n_in == 0) return cudaSuccess;
+  const unsigned long long chunks = (a.n_in + 31ull) / 32ull;
+  const unsigned long long blocks_needed = (chunks + kWarps - 1) / kWarps;
+  int grid = a.grid;
+  if (grid <= 0) {
+    static thread_local int cached_dev = -1, cached_grid[3][3] = {{0}};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int kc = (int)a.kc;
+    const int wi = kWarps == 2 ? 0 : (kWarps == 4 ? 1 : 2);
+    if (cached_dev != dev) {
+      for (auto& r : cached_grid)
+        for (int& x : r) x = 0;
+      cached_dev = dev;
+    }
+    if (cached_grid[kc][wi] == 0) {
+      int sms = 0, per_sm = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_insert_kernel<K, kWarps>, kWarps * 32, 0);
+      cached_grid[kc][wi] = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    grid = cached_grid[kc][wi];
+  }
+  if ((unsigned long long)grid > blocks_needed) grid = (int)blocks_needed;
+  expand_insert_kernel<K, kWarps><<<grid, kWarps * 32, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_expand_k(const ExpandLaunch& a, cudaStream_t s) {
+  switch (a.block_threads) {
+    case 64: return launch_expand_t<K, 2>(a, s);
+    case 256: return launch_expand_t<K, 8>(a, s);
+    default: return launch_expand_t<K, 4>(a, s);
+  }
+}
+
+// The 128-bit queue of 8 warps would exceed the 48 KB static shared limit.
+template <>
+cudaError_t launch_expand_k<K128>(const ExpandLaunch& a, cudaStream_t s) {
+  return a.block_threads == 64 ? launch_expand_t<K128, 2>(a, s) : launch_expand_t<K128, 4>(a, s);
+}
+
+// ---------------------------------------------------------------- clearing
+__global__ void clear_kernel(uint4* __restrict__ t, size_t n16, LevelCounters* ctr) {
+  if (blockIdx.x == 0 && threadIdx.x < sizeof(LevelCounters) / sizeof(unsigned long long))
+    reinterpret_cast<unsigned long long*>(ctr)[threadIdx.x] = 0ull;
+  const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) t[i] = ones;
+}
+
+// ------------------------------------------------------------ fingerprints
+template <class K>
+__global__ void fingerprint_kernel(const K* __restrict__ keys, unsigned long long count, LevelCounters* ctr) {
+  unsigned long long s = 0, x = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const unsigned long long f = kfingerprint(keys[i]);
+    s += f;
+    x ^= f;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    s += __shfl_xor_sync(kFull, s, d);
+    x ^= __shfl_xor_sync(kFull, x, d);
+  }
+  if ((threadIdx.x & 31) == 0 && (s | x)) {
+    atomicAdd(&ctr->fp_sum, s);
+    atomicXor(&ctr->fp_xor, x);
+  }
+}
+
+// ------------------------------------------------------------ backward walk
+template <class K>
+__global__ void walk_init_kernel(const K* keys, K* walk, int last) {
+  walk[last] = keys[0];
+}
+
+template <class K>
+__global__ void walk_step_kernel(const K* __restrict__ keys, const uint8_t* __restrict__ pred,
+                                 unsigned long long count, K* walk, int j, int32_t* order) {
+  const K target = walk[j];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    if (keys[i] == target) {
+      const int v = pred[i];
+      order[j - 1] = v;
+      walk[j - 1] = target & ~kbit<K>(v);
+    }
+  }
+}
+
+template <class K>
+__global__ void walk_finish_kernel(const K* walk, int last, int n, int32_t* order) {
+  const K fin = walk[last];
+  int pos = last;
+  for (int v = 0; v < n; ++v)
+    if (!ktest(fin, v)) order[pos++] = v;
+}
+
+// --------------------------------------------------- tree decomposition
+__global__ void td_kernel(const unsigned long long* __restrict__ adj64, int n, int words64,
+                          const int32_t* __restrict__ order, int32_t* parent, unsigned long long* bags) {
+  __shared__ K128 sAdj[128];
+  __shared__ int sPos[128];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sAdj[i] = K128{adj64[(size_t)i * words64], words64 > 1 ? adj64[(size_t)i * words64 + 1] : 0ull};
+    sPos[i] = n;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int o = order[i];
+    if (o >= 0 && o < n) sPos[o] = i;  // a malformed order never indexes out of range
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    const int pv = sPos[v];
+    K128 prefix = kzero<K128>();
+    for (int u = 0; u < n; ++u)
+      if (sPos[u] < pv) prefix |= kbit<K128>(u);
+    K128 q = sAdj[v] & ~prefix;
+    K128 vis = sAdj[v] & prefix;
+    K128 front = vis;
+    while (!kempty(front)) {
+      const int u = klowest(front);
+      front = kdrop_lowest(front);
+      const K128 r = sAdj[u];
+      q |= r & ~prefix;
+      const K128 nw = r & prefix & ~vis;
+      vis |= nw;
+      front |= nw;
+    }
+    q &= ~kbit<K128>(v);
+    const K128 bag = q | kbit<K128>(v);
+    bags[(size_t)v * words64] = bag.lo;
+    if (words64 > 1) bags[(size_t)v * words64 + 1] = bag.hi;
+    int best = -1;
+    K128 t = q;
+    while (!kempty(t)) {
+      const int u = klowest(t);
+      t = kdrop_lowest(t);
+      if (best < 0 || sPos[u] < sPos[best]) best = u;
+    }
+    if (best < 0) best = (pv >= n - 1) ? -1 : order[n - 1];
+    parent[v] = best;
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+int stream_grid(unsigned long long work, int per_block) {
+  unsigned long long g = (work + per_block - 1) / per_block;
+  const unsigned long long cap = (unsigned long long)sm_count() * 8ull;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_expand(const ExpandLaunch& a, cudaStream_t s) {
+  switch (a.kc) {
+    case kKey32: return launch_expand_k<uint32_t>(a, s);
+    case kKey64: return launch_expand_k<unsigned long long>(a, s);
+    default: return launch_expand_k<K128>(a, s);
+  }
+}
+
+cudaError_t launch_clear(void* table, size_t table_bytes, LevelCounters* ctr, cudaStream_t s) {
+  const size_t n16 = table_bytes / 16;
+  clear_kernel<<<stream_grid(n16 > 0 ? n16 : 1, 256 * 4), 256, 0, s>>>(static_cast<uint4*>(table), n16, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fingerprint(KeyClass kc, const void* keys, unsigned long long count, LevelCounters* ctr,
+                               cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const int g = stream_grid(count, 256 * 4);
+  switch (kc) {
+    case kKey32: fingerprint_kernel<uint32_t><<<g, 256, 0, s>>>(static_cast<const uint32_t*>(keys), count, ctr); break;
+    case kKey64:
+      fingerprint_kernel<unsigned long long><<<g, 256, 0, s>>>(static_cast<const unsigned long long*>(keys), count, ctr);
+      break;
+    default: fingerprint_kernel<K128><<<g, 256, 0, s>>>(static_cast<const K128*>(keys), count, ctr); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_init(KeyClass kc, const void* keys, void* walk, int last, cudaStream_t s) {
+  switch (kc) {
+    case kKey32: walk_init_kernel<uint32_t><<<1, 1, 0, s>>>(static_cast<const uint32_t*>(keys), static_cast<uint32_t*>(walk), last); break;
+    case kKey64:
+      walk_init_kernel<unsigned long long><<<1, 1, 0, s>>>(static_cast<const unsigned long long*>(keys),
+                                                           static_cast<unsigned long long*>(walk), last);
+      break;
+    default: walk_init_kernel<K128><<<1, 1, 0, s>>>(static_cast<const K128*>(keys), static_cast<K128*>(walk), last); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_step(KeyClass kc, const void* keys, const uint8_t* pred, unsigned long long count, void* walk,
+                             int j, int32_t* order, cudaStream_t s) {
+  const int g = stream_grid(count > 0 ? count : 1, 256 * 4);
+  switch (kc) {
+    case kKey32:
+      walk_step_kernel<uint32_t><<<g, 256, 0, s>>>(static_cast<const uint32_t*>(keys), pred, count,
+                                                   static_cast<uint32_t*>(walk), j, order);
+      break;
+    case kKey64:
+      walk_step_kernel<unsigned long long><<<g, 256, 0, s>>>(static_cast<const unsigned long long*>(keys), pred, count,
+                                                             static_cast<unsigned long long*>(walk), j, order);
+      break;
+    default:
+      walk_step_kernel<K128><<<g, 256, 0, s>>>(static_cast<const K128*>(keys), pred, count, static_cast<K128*>(walk), j,
+                                               order);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_finish(KeyClass kc, const void* walk, int last, int n, int32_t* order, cudaStream_t s) {
+  switch (kc) {
+    case kKey32: walk_finish_kernel<uint32_t><<<1, 1, 0, s>>>(static_cast<const uint32_t*>(walk), last, n, order); break;
+    case kKey64:
+      walk_finish_kernel<unsigned long long><<<1, 1, 0, s>>>(static_cast<const unsigned long long*>(walk), last, n, order);
+      break;
+    default: walk_finish_kernel<K128><<<1, 1, 0, s>>>(static_cast<const K128*>(walk), last, n, order); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_td(const unsigned long long* adj64, int n, int words64, const int32_t* order, int32_t* parent,
+                      unsigned long long* bags, cudaStream_t s) {
+  td_kernel<<<1, 128, 0, s>>>(adj64, n, words64, order, parent, bags);
+  return cudaGetLastError();
+}
+
+}  // namespace tw

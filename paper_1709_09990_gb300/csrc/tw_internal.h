@@ -1,0 +1,92 @@
+// Interfaces between the translation units of libtw (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace tw {
+
+// Width class of the state bitsets.
+enum KeyClass : int { kKey32 = 0, kKey64 = 1, kKey128 = 2 };
+
+inline KeyClass key_class_for(int n) { return n <= 32 ? kKey32 : (n <= 64 ? kKey64 : kKey128); }
+inline size_t key_bytes(KeyClass c) { return c == kKey32 ? 4 : (c == kKey64 ? 8 : 16); }
+
+// Device-side counters of one level expansion (one per context, 64-byte
+// aligned in device memory and mirrored in pinned host memory).
+struct LevelCounters {
+  unsigned long long out_count;  // states appended to L_{i+1} (counts past capacity too)
+  unsigned long long feasible;   // candidates (S, v) with |Q(S, v)| <= k
+  unsigned long long fp_sum;     // sum of fingerprints of L_{i+1}
+  unsigned long long fp_xor;     // xor of fingerprints of L_{i+1}
+  unsigned int overflow;         // bit 0: output list full, bit 1: probe limit reached
+  unsigned int pad[7];
+};
+
+// One level i -> i+1 of Listing 1 (arXiv 1709.09990, Section 3.1).
+struct ExpandLaunch {
+  KeyClass kc;
+  const void* in_keys;           // |L_i| keys
+  unsigned long long n_in;
+  const void* adj;               // n rows, one key each
+  int n;
+  int k;
+  void* table;                   // power-of-two slots, all set to the empty key
+  unsigned long long table_slots;
+  int max_probes;
+  void* out_keys;                // L_{i+1} keys (capacity out_cap)
+  uint8_t* out_pred;             // predecessor vertex of each L_{i+1} state
+  unsigned long long out_cap;
+  LevelCounters* ctr;
+  int block_threads;             // 64, 128 or 256
+  int grid;                      // 0 = derived from the occupancy of this device
+};
+
+cudaError_t launch_expand(const ExpandLaunch& a, cudaStream_t s);
+
+// Sets every slot of a table to the empty key (all ones) and zeroes ctr.
+cudaError_t launch_clear(void* table, size_t table_bytes, LevelCounters* ctr, cudaStream_t s);
+
+// Adds the fingerprints of count keys into ctr->fp_sum / fp_xor.
+cudaError_t launch_fingerprint(KeyClass kc, const void* keys, unsigned long long count,
+                               LevelCounters* ctr, cudaStream_t s);
+
+// One step of the backward walk: finds walk[j] among the count keys of level
+// j, writes its predecessor vertex v to order[j-1] and walk[j-1] = walk[j]
+// minus v.  walk holds one key per level.
+cudaError_t launch_walk_step(KeyClass kc, const void* keys, const uint8_t* pred,
+                             unsigned long long count, void* walk, int j, int32_t* order,
+                             cudaStream_t s);
+
+// walk[last] = keys[0] (first state of the final level).
+cudaError_t launch_walk_init(KeyClass kc, const void* keys, void* walk, int last, cudaStream_t s);
+
+// order[last..n-1] = the vertices outside walk[last], in increasing order.
+cudaError_t launch_walk_finish(KeyClass kc, const void* walk, int last, int n, int32_t* order,
+                               cudaStream_t s);
+
+// Tree decomposition from an ordering (one thread per vertex):
+// bag(v) = {v} u Q(prefix(v), v), parent(v) = first vertex of Q after v in
+// the order (or the last vertex; the last vertex is the root).
+// adj64 / bags: n rows x words64 uint64.
+cudaError_t launch_td(const unsigned long long* adj64, int n, int words64, const int32_t* order,
+                      int32_t* parent, unsigned long long* bags, cudaStream_t s);
+
+// Bounds (one warp per graph): out[4*g + 0..3] = MMD, MMD+, min-degree width,
+// min-fill width.  Graph g: n[g] rows of ceil(n[g]/64) words at row_offset[g].
+cudaError_t launch_bounds(const unsigned long long* adj, const int32_t* n, const int64_t* row_offset,
+                          int num_graphs, int32_t* out, float* feats, cudaStream_t s);
+
+// Network kernels.
+cudaError_t launch_mlp_forward(const float* params, const float* x, int batch, float* yhat, cudaStream_t s);
+cudaError_t launch_mlp_grad(const float* params, const float* x, const float* y, int batch,
+                            float* grad, float* partial, int partial_blocks, cudaStream_t s);
+cudaError_t launch_mlp_adam(float* params, const float* grad, float* m, float* v, int t, float lr,
+                            float beta1, float beta2, float eps, cudaStream_t s);
+cudaError_t launch_mlp_train(float* params, float* m, float* v, const float* x, const float* y,
+                             int batch_total, int minibatch, int epochs, const int32_t* perm,
+                             float lr, float* loss_out, cudaStream_t s);
+
+}  // namespace tw

@@ -1,0 +1,31 @@
+"""Shared helpers of the GPU tests (test code only)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_09990_gb300 import graphgen as gg
+
+
+def context(**kw):
+    from paper_1709_09990_gb300 import native
+    return native.Context(device=0, **kw)
+
+
+def assert_decide_matches(ctx, adj, k, check_order=True):
+    exp = oracle.decide(adj, k)
+    got = ctx.decide(adj, k=k, want_order=check_order)
+    st = got["stats"]
+    assert got["yes"] == exp["yes"], (k, got["yes"], exp["yes"])
+    assert st["levels"] == exp["levels"], (k, st["level_size"], exp["level_size"])
+    assert st["level_size"] == exp["level_size"], k
+    assert st["fp_sum"] == exp["fp_sum"], k
+    assert st["fp_xor"] == exp["fp_xor"], k
+    assert st["states_expanded"] == exp["states_expanded"]
+    assert st["candidates"] == exp["candidates"]
+    assert st["feasible"] == exp["feasible"]
+    if check_order and got["yes"]:
+        order = got["order"].tolist()
+        assert sorted(order) == list(range(len(adj)))
+        assert oracle.width_q(adj, order) <= k
+        assert oracle.width_elim(adj, order) <= k
+    return got, exp
