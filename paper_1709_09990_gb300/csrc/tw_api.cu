@@ -399,7 +399,12 @@ int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order,
   if (rc) return rc;
   DecideResult R;
   rc = run_decide(c, kc, g.n, k, order != nullptr, &R);
-  if (rc) return rc;
+  if (rc) {
+    // the levels completed before the failure are still reported
+    fill_stats(R, k, st, true);
+    if (st) st->seconds = t.seconds();
+    return rc;
+  }
   if (R.yes && order) {
     rc = reconstruct(c, kc, g.n, R);
     if (rc) return rc;

@@ -171,7 +171,10 @@ class Context:
         order = order_out if order_out is not None else (np.full(n, -1, np.int32) if want_order else None)
         rc = lib().tw_decide(self._h, _ptr(rows), n, k, ctypes.addressof(yes), _ptr(order), ctypes.byref(st))
         if raise_on_error:
-            _check(rc, "tw_decide")
+            if rc != TW_OK:
+                err = TwError(rc, "tw_decide")
+                err.stats = st.as_dict()
+                raise err
         return {"status": rc, "yes": bool(yes.value == 1), "order": order, "stats": st.as_dict()}
 
     def decide_u32(self, adj_rows_u32: np.ndarray, n: int, k: int, want_order: bool = False):

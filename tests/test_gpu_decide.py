@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import bounds as obounds
 from paper_1709_09990_gb300 import graphgen as gg
 from tests.gpu_util import assert_decide_matches, context
 
@@ -58,28 +59,31 @@ def test_random_small_u32(ctx, seed):
             assert_decide_matches(ctx, adj, k)
 
 
-@pytest.mark.parametrize("family", ["gnp_dense", "pktree", "rgg"])
-def test_u64_class(ctx, family):
-    # 33 <= n <= 64: sizes whose oracle runs take seconds
-    for s in range(3):
-        if family == "gnp_dense":
-            adj = gg.gnp(40 + 4 * s, 0.6, 10 + s)
-        elif family == "pktree":
-            adj = gg.partial_ktree(36 + s, 3, 20 + s)
-        else:
-            adj = gg.rgg(34 + s, 0.2, 30 + s)
-        tw = oracle.solve(adj, want_order=False)["tw"]
-        for k in (tw - 1, tw):
-            assert_decide_matches(ctx, adj, k)
+# 33 <= n <= 64, chosen so that each oracle run takes seconds
+U64_CASES = [("gnp", 44, 0.5, 4), ("partial_ktree", 34, 8, 8), ("gnp", 50, 0.6, 11), ("gnp", 60, 0.7, 12),
+             ("gnp", 64, 0.75, 14)]
 
 
-def test_u128_class(ctx):
+@pytest.mark.parametrize("case", U64_CASES, ids=lambda c: f"{c[0]}{c[1]}")
+def test_u64_class(ctx, case):
+    fam, n, par, seed = case
+    adj = getattr(gg, fam)(n, par, seed)
+    lb = max(obounds.mmd(adj), obounds.mmd_plus(adj))
+    tw = oracle.solve(adj, k_start=lb, want_order=False)["tw"]
+    for k in (tw - 1, tw):
+        assert_decide_matches(ctx, adj, k)
+
+
+@pytest.mark.parametrize("case", [(66, 0.85), (70, 0.8), (80, 0.9), (90, 0.88), (100, 0.93), (128, 0.96)],
+                         ids=lambda c: f"n{c[0]}")
+def test_u128_class(ctx, case):
     # 65 <= n <= 128, dense enough that few levels are needed
-    for s, (n, p) in enumerate([(66, 0.85), (80, 0.9), (100, 0.93), (128, 0.96)]):
-        adj = gg.gnp(n, p, 40 + s)
-        tw = oracle.solve(adj, k_start=n - 12, want_order=False)["tw"]
-        for k in (tw - 1, tw):
-            assert_decide_matches(ctx, adj, k)
+    n, p = case
+    adj = gg.gnp(n, p, 40 + n)
+    lb = max(obounds.mmd(adj), obounds.mmd_plus(adj))
+    tw = oracle.solve(adj, k_start=lb, want_order=False)["tw"]
+    for k in (tw - 1, tw):
+        assert_decide_matches(ctx, adj, k)
 
 
 def test_u128_sparse_across_word_boundary(ctx):
