@@ -65,7 +65,9 @@ typedef struct {
   int ub_shortcut;        /* tw_solve: accept the heuristic upper bound when the
                              lower bound meets it, without a decide run (0 = off) */
   int graph_levels;       /* 1 = drive levels through a captured CUDA graph       */
-  int reserved[7];        /* must be zero                                         */
+  int time_kernels;       /* 1 = time every expand launch with CUDA events on the
+                             context's stream (fills expand_seconds)              */
+  int reserved[6];        /* must be zero                                         */
 } tw_config;
 
 /* Per-call statistics.  Level arrays describe the last decide run. */
@@ -84,6 +86,15 @@ typedef struct {
   uint64_t decide_runs;                     /* decide runs in this call         */
   uint64_t level_retries;                   /* levels re-run after growing      */
   double seconds;                           /* wall time of the call            */
+  uint64_t kernel_launches;                 /* libtw kernels launched by the call */
+  uint64_t expand_launches;                 /* expand+insert launches           */
+  double expand_seconds;                    /* summed CUDA-event time of those
+                                               launches (time_kernels only)     */
+  double expand_bytes;                      /* algorithmic bytes of those launches:
+                                               sum over levels of (|L_i| + F_i +
+                                               2|L_{i+1}|) * w + |L_{i+1}|, with
+                                               w the key bytes and F_i the
+                                               feasible candidates             */
 } tw_stats;
 
 /* fp(S) = mix(w0 ^ mix(w1)), mix = the splitmix64 output function, over the

@@ -48,6 +48,8 @@ struct tw_ctx {
   LevelCounters* d_ctr = nullptr;
   LevelCounters* h_ctr = nullptr;
   int sms = 0;
+  unsigned long long launches = 0;       // libtw kernels launched so far
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // expand timing (time_kernels)
 };
 
 namespace {
@@ -61,6 +63,13 @@ constexpr size_t kSmallBytes = 1 << 20;
       cudaGetLastError();                        \
       return TW_ERR_CUDA;                        \
     }                                            \
+  } while (0)
+
+// Launches a libtw kernel and counts it.
+#define TW_LAUNCH(c, expr) \
+  do {                     \
+    TW_CK(expr);           \
+    ++(c)->launches;       \
   } while (0)
 
 struct Timer {
@@ -235,6 +244,8 @@ struct DecideResult {
   int yes = 0;
   std::vector<LevelRec> levels;
   unsigned long long states_expanded = 0, candidates = 0, feasible = 0, peak_bytes = 0, retries = 0;
+  unsigned long long expand_launches = 0;
+  double expand_seconds = 0.0, expand_bytes = 0.0;
   std::vector<unsigned long long> fp_sum, fp_xor;
 };
 
@@ -243,6 +254,10 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
   const size_t w = key_bytes(kc);
   SmallLayout L;
   R->levels.clear();
+  R->yes = 0;
+  R->states_expanded = R->candidates = R->feasible = R->peak_bytes = R->retries = 0;
+  R->expand_launches = 0;
+  R->expand_seconds = R->expand_bytes = 0.0;
   R->fp_sum.assign(1, 0ull);  // fp of the empty set is 0
   R->fp_xor.assign(1, 0ull);
   int rc = grow(c, &c->keys, 64 * w, 0);
@@ -290,7 +305,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       if (rc) return rc;
       rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)live_end);
       if (rc) return rc;
-      TW_CK(launch_clear(c->table.ptr, slots * w, c->d_ctr, c->stream));
+      TW_LAUNCH(c, launch_clear(c->table.ptr, slots * w, c->d_ctr, c->stream));
       ExpandLaunch a;
       a.kc = kc;
       a.in_keys = static_cast<char*>(c->keys.ptr) + cur.off * w;
@@ -307,10 +322,15 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       a.ctr = c->d_ctr;
       a.block_threads = c->cfg.block_threads;
       a.grid = 0;
-      TW_CK(launch_expand(a, c->stream));
+      const bool timed = c->cfg.time_kernels != 0;
+      if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
+      TW_LAUNCH(c, launch_expand(a, c->stream));
+      if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
       TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
       TW_CK(cudaStreamSynchronize(c->stream));
       const LevelCounters h = *c->h_ctr;
+      float ms = 0.f;
+      if (timed) TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
       const bool table_full = (h.overflow & 2u) || h.out_count * 100ull > slots * 90ull;
       if (table_full) {
         const double grown = std::max((double)out_cap * 2.0, (double)h.out_count * 1.5);
@@ -328,6 +348,9 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       nxt.off = off;
       nxt.count = h.out_count;
       R->feasible += h.feasible;
+      R->expand_launches += 1;
+      R->expand_seconds += (double)ms * 1e-3;
+      R->expand_bytes += (double)(cur.count + h.feasible + 2ull * h.out_count) * (double)w + (double)h.out_count;
       const unsigned long long live_states = keep_levels ? kept_states + nxt.count : cur.count + nxt.count;
       R->peak_bytes = std::max<unsigned long long>(R->peak_bytes, live_states * (w + 1) + slots * w);
       break;
@@ -337,7 +360,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
     if (keep_levels) kept_states += nxt.count;
     R->levels.push_back(nxt);
     if (c->cfg.fingerprints) {
-      TW_CK(launch_fingerprint(kc, static_cast<char*>(c->keys.ptr) + nxt.off * w, nxt.count, c->d_ctr, c->stream));
+      TW_LAUNCH(c, launch_fingerprint(kc, static_cast<char*>(c->keys.ptr) + nxt.off * w, nxt.count, c->d_ctr, c->stream));
       TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
       TW_CK(cudaStreamSynchronize(c->stream));
       R->fp_sum.push_back(c->h_ctr->fp_sum);
@@ -359,12 +382,12 @@ int reconstruct(tw_ctx* c, KeyClass kc, int n, const DecideResult& R) {
   void* walk = small_at(c, L.walk);
   char* keys = static_cast<char*>(c->keys.ptr);
   const uint8_t* pred = static_cast<const uint8_t*>(c->pred.ptr);
-  TW_CK(launch_walk_init(kc, keys + R.levels[last].off * w, walk, last, c->stream));
+  TW_LAUNCH(c, launch_walk_init(kc, keys + R.levels[last].off * w, walk, last, c->stream));
   for (int j = last; j >= 1; --j) {
     const LevelRec& lr = R.levels[j];
-    TW_CK(launch_walk_step(kc, keys + lr.off * w, pred + lr.off, lr.count, walk, j, d_order, c->stream));
+    TW_LAUNCH(c, launch_walk_step(kc, keys + lr.off * w, pred + lr.off, lr.count, walk, j, d_order, c->stream));
   }
-  TW_CK(launch_walk_finish(kc, walk, last, n, d_order, c->stream));
+  TW_LAUNCH(c, launch_walk_finish(kc, walk, last, n, d_order, c->stream));
   return TW_OK;
 }
 
@@ -373,6 +396,8 @@ void fill_stats(const DecideResult& R, int k, tw_stats* st, bool reset_totals) {
   if (reset_totals) {
     st->states_expanded = st->candidates = st->feasible = st->peak_frontier_bytes = 0;
     st->decide_runs = st->level_retries = 0;
+    st->expand_launches = 0;
+    st->expand_seconds = st->expand_bytes = 0.0;
   }
   st->levels = (int)R.levels.size();
   st->k = k;
@@ -388,10 +413,14 @@ void fill_stats(const DecideResult& R, int k, tw_stats* st, bool reset_totals) {
   st->peak_frontier_bytes = std::max<uint64_t>(st->peak_frontier_bytes, R.peak_bytes);
   st->decide_runs += 1;
   st->level_retries += R.retries;
+  st->expand_launches += R.expand_launches;
+  st->expand_seconds += R.expand_seconds;
+  st->expand_bytes += R.expand_bytes;
 }
 
 int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order, tw_stats* st) {
   Timer t;
+  const unsigned long long launches0 = c->launches;
   if (k < 0 || yes == nullptr) return TW_ERR_INVALID;
   TW_CK(cudaSetDevice(c->device));
   const KeyClass kc = key_class_for(g.n);
@@ -416,7 +445,10 @@ int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order,
   int y = R.yes;
   rc = put(c, yes, &y, sizeof(int));
   if (rc) return rc;
-  if (st) st->seconds = t.seconds();
+  if (st) {
+    st->seconds = t.seconds();
+    st->kernel_launches = c->launches - launches0;
+  }
   return TW_OK;
 }
 
@@ -429,7 +461,7 @@ int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]) {
   const int64_t off = 0;
   TW_CK(cudaMemcpyAsync(d_n, &nn, 4, cudaMemcpyHostToDevice, c->stream));
   TW_CK(cudaMemcpyAsync(d_off, &off, 8, cudaMemcpyHostToDevice, c->stream));
-  TW_CK(launch_bounds(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), d_n, d_off, 1, d_out,
+  TW_LAUNCH(c, launch_bounds(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), d_n, d_off, 1, d_out,
                       nullptr, c->stream));
   TW_CK(cudaMemcpyAsync(out, d_out, 16, cudaMemcpyDeviceToHost, c->stream));
   TW_CK(cudaStreamSynchronize(c->stream));
@@ -439,6 +471,7 @@ int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]) {
 int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int32_t* td_parent, uint64_t* td_bags,
                 tw_stats* st, int k_first) {
   Timer t;
+  const unsigned long long launches0 = c->launches;
   TW_CK(cudaSetDevice(c->device));
   const KeyClass kc = key_class_for(g.n);
   int rc = upload_graph(c, g, kc);
@@ -452,6 +485,8 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
   if (st) {
     st->states_expanded = st->candidates = st->feasible = st->peak_frontier_bytes = 0;
     st->decide_runs = st->level_retries = 0;
+    st->expand_launches = 0;
+    st->expand_seconds = st->expand_bytes = 0.0;
   }
   int tw = -1;
   DecideResult R;
@@ -476,7 +511,7 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
     if (rc) return rc;
     int32_t* d_order = reinterpret_cast<int32_t*>(small_at(c, L.order));
     if (td_parent || td_bags) {
-      TW_CK(launch_td(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), g.n, g.words, d_order,
+      TW_LAUNCH(c, launch_td(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), g.n, g.words, d_order,
                       reinterpret_cast<int32_t*>(small_at(c, L.parent)),
                       reinterpret_cast<unsigned long long*>(small_at(c, L.bags)), c->stream));
     }
@@ -490,7 +525,10 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
   TW_CK(cudaStreamSynchronize(c->stream));
   rc = put(c, tw_out, &tw, sizeof(int));
   if (rc) return rc;
-  if (st) st->seconds = t.seconds();
+  if (st) {
+    st->seconds = t.seconds();
+    st->kernel_launches = c->launches - launches0;
+  }
   return TW_OK;
 }
 
@@ -718,6 +756,7 @@ int tw_create(tw_ctx** out, const tw_config* cfg) {
   if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_ctr), sizeof(LevelCounters), cudaHostAllocDefault) != cudaSuccess)
     return fail(TW_ERR_CUDA);
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return fail(TW_ERR_CUDA);
   *out = c;
   return TW_OK;
 }
@@ -730,6 +769,8 @@ void tw_destroy(tw_ctx* c) {
     if (b->ptr) cudaFree(b->ptr);
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;

@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("fingerprints", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t),
                 ("stream", ctypes.c_void_p), ("block_threads", ctypes.c_int), ("table_load_pct", ctypes.c_int),
                 ("max_probes", ctypes.c_int), ("ub_shortcut", ctypes.c_int), ("graph_levels", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("time_kernels", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class Stats(ctypes.Structure):
@@ -45,7 +45,9 @@ class Stats(ctypes.Structure):
                 ("states_expanded", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("feasible", ctypes.c_uint64), ("peak_frontier_bytes", ctypes.c_uint64),
                 ("decide_runs", ctypes.c_uint64), ("level_retries", ctypes.c_uint64),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
+                ("expand_launches", ctypes.c_uint64), ("expand_seconds", ctypes.c_double),
+                ("expand_bytes", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         L = self.levels
@@ -54,7 +56,9 @@ class Stats(ctypes.Structure):
                 "states_expanded": int(self.states_expanded), "candidates": int(self.candidates),
                 "feasible": int(self.feasible), "peak_frontier_bytes": int(self.peak_frontier_bytes),
                 "decide_runs": int(self.decide_runs), "level_retries": int(self.level_retries),
-                "seconds": float(self.seconds)}
+                "seconds": float(self.seconds), "kernel_launches": int(self.kernel_launches),
+                "expand_launches": int(self.expand_launches), "expand_seconds": float(self.expand_seconds),
+                "expand_bytes": float(self.expand_bytes)}
 
 
 _lib = None
@@ -130,7 +134,7 @@ class Context:
 
     def __init__(self, device: int = 0, fingerprints: bool = False, mem_cap_bytes: int = 0,
                  stream: int = 0, block_threads: int = 0, table_load_pct: int = 0, max_probes: int = 0,
-                 ub_shortcut: bool = False):
+                 ub_shortcut: bool = False, time_kernels: bool = False):
         cfg = Config()
         cfg.device = device
         cfg.fingerprints = int(fingerprints)
@@ -140,6 +144,7 @@ class Context:
         cfg.table_load_pct = table_load_pct
         cfg.max_probes = max_probes
         cfg.ub_shortcut = int(ub_shortcut)
+        cfg.time_kernels = int(time_kernels)
         h = _vp()
         _check(lib().tw_create(ctypes.byref(h), ctypes.byref(cfg)), "tw_create")
         self._h = h

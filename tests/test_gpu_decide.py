@@ -120,13 +120,17 @@ def test_rgg40_full_k6_golden(ctx):
 
 def test_closed_form_levels(ctx):
     import math
-    for n in (5, 17, 33, 40):
+    for n in (5, 17, 22):
         got = ctx.decide([0] * n, k=0)
         assert got["stats"]["level_size"] == [math.comb(n, i) for i in range(n)]
         got = ctx.decide(gg.cycle(n), k=2)
         assert got["stats"]["level_size"] == [math.comb(n, i) for i in range(n - 2)]
-        got = ctx.decide(gg.path(n), k=1)
+        got = ctx.decide(gg.star(n), k=1)
+        assert got["stats"]["level_size"] == [math.comb(n - 1, i) for i in range(n - 1)]
+    for n in (5, 17, 33, 40, 64, 65, 100, 128):
+        got = ctx.decide(gg.path(n), k=1, want_order=True)
         assert got["stats"]["level_size"] == [i + 1 for i in range(n - 1)]
+        assert oracle.width_q(gg.path(n), got["order"].tolist()) == 1
         got = ctx.decide(gg.complete(n), k=n - 2)
         assert got["stats"]["level_size"] == [1, 0] and not got["yes"]
 

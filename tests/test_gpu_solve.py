@@ -37,8 +37,8 @@ def test_solve_random(ctx, seed):
 
 
 def test_solve_families(ctx):
-    cases = [gg.grid(4, 5), gg.complete_bipartite(4, 6), gg.cycle(40), gg.random_tree(50, 3), gg.complete(12),
-             gg.ktree(45, 4, 2), gg.partial_ktree(50, 5, 3), [0] * 7]
+    cases = [gg.grid(4, 5), gg.complete_bipartite(4, 6), gg.cycle(20), gg.random_tree(20, 3), gg.complete(12),
+             gg.ktree(26, 4, 2), gg.partial_ktree(26, 5, 3), [0] * 7]
     closed = [4, 4, 2, 1, 11, 4, None, 0]
     for adj, tw in zip(cases, closed):
         sol = ctx.solve(adj, want_order=True, want_td=True)
