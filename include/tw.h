@@ -190,6 +190,36 @@ int tw_mlp_adam(tw_ctx* ctx, float* params, const float* grad, float* m, float* 
 int tw_mlp_train(tw_ctx* ctx, float* params, const float* x, const float* y, int batch_total,
                  int minibatch, int epochs, const int32_t* perm, float lr, float* loss_out);
 
+/* One wavefront level that allocates nothing (the paper has no counterpart;
+ * this exists for callers that cannot let a library call cudaMalloc, e.g. a
+ * host that has already given the device's memory to its own pool, or a
+ * latency-critical loop that cannot take the device-wide synchronisation of
+ * cudaMalloc/cudaFree).
+ * It runs the expand+insert kernel of tw_decide for one level i -> i+1 on the
+ * current device and the given stream (NULL = the legacy default stream).
+ * Its hash table and counters live in a fixed static device array of 16 MiB
+ * + 256 bytes inside libtw, held by every GPU that loads the library until
+ * the process exits.
+ *   d_in_keys  : device, n_in 64-bit keys of level i (bit v = vertex v).
+ *   d_adj      : device, n 64-bit adjacency rows, n <= 64.
+ *   k          : the bound.
+ *   d_out_keys : device, out_cap keys of level i+1 (written in any order).
+ *   d_out_pred : device, out_cap bytes: the vertex added to each output key.
+ *   out_cap    : at most TW_STATIC_MAX_STATES; larger values return
+ *                TW_ERR_INVALID without running.
+ *   out_count  : host, receives |L_{i+1}| (also when it exceeds out_cap).
+ * Returns TW_OK; TW_ERR_CAPACITY when level i+1 has more than out_cap states
+ * (or the fixed table overflows) - the output is then incomplete;
+ * TW_ERR_INVALID for host pointers, n > 64 or out_cap too large;
+ * TW_ERR_CUDA.  The first call on a device resolves the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call reuses the same array: calls that overlap on the GPU
+ * (other streams, other host threads) race and corrupt each other. */
+#define TW_STATIC_MAX_STATES (1ull << 20)
+int tw_expand_level_static(const uint64_t* d_in_keys, uint64_t n_in, const uint64_t* d_adj, int n, int k,
+                           uint64_t* d_out_keys, uint8_t* d_out_pred, uint64_t out_cap,
+                           uint64_t* out_count, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* tw_strerror(int status);
 
