@@ -276,19 +276,27 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
   unsigned long long kept_states = 1;  // states of kept levels (keep mode)
   for (int i = 0; i <= n - k - 2; ++i) {
     const LevelRec cur = R->levels[i];
+    // Upper bounds on |L_{i+1}|: every state has n-i extensions, and there
+    // are C(n, i+1) sets of that size.
+    const double bound = std::min((double)cur.count * (double)(n - i), binom(n, i + 1)) + 1.0;
+    // Prediction from the previous level's growth; the table gets 25% slack
+    // over the prediction at the target load, the output list room for the
+    // worst case (clamped), so output overflow is rare.
     double est;
     if (i == 0) {
       est = n;
     } else {
       const double prev = (double)R->levels[i - 1].count;
       double r = prev > 0 ? (double)cur.count / prev : 1.0;
-      r = std::min(std::max(r, 0.5), (double)(n - i));
-      est = (double)cur.count * r * 1.5 + 256.0;
-      est = std::min(est, (double)cur.count * (double)(n - i) + 1.0);
-      est = std::min(est, binom(n, i + 1) + 1.0);
+      r = std::min(std::max(r, 0.25), (double)(n - i));
+      est = (double)cur.count * r;
     }
-    unsigned long long out_cap = (unsigned long long)std::ceil(est);
-    unsigned long long slots = next_pow2((unsigned long long)std::ceil(est * 100.0 / load_pct));
+    double table_est = std::min(est * 1.25 + 1024.0, bound);
+    const double mem_states = (double)c->mem_cap / (double)(w + 1);
+    unsigned long long out_cap =
+        (unsigned long long)std::ceil(std::min(bound, std::max(table_est * 3.0, std::min(bound, mem_states / 4))));
+    unsigned long long slots = std::max<unsigned long long>(
+        64ull, (unsigned long long)std::ceil(table_est * 100.0 / load_pct));
     LevelRec nxt;
     for (int attempt = 0;; ++attempt) {
       if (attempt > 40) return TW_ERR_CAPACITY;
@@ -299,13 +307,14 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
         off = (out_cap <= cur.off) ? 0ull : cur.off + cur.count;
       }
       const unsigned long long live_end = cur.off + cur.count;  // data to keep on growth
-      rc = grow(c, &c->table, slots * w, 0);
+      const size_t table_bytes = (slots * w + 15) & ~size_t(15);
+      rc = grow(c, &c->table, table_bytes, 0);
       if (rc) return rc;
       rc = grow(c, &c->keys, (size_t)(off + out_cap) * w, (size_t)live_end * w);
       if (rc) return rc;
       rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)live_end);
       if (rc) return rc;
-      TW_LAUNCH(c, launch_clear(c->table.ptr, slots * w, c->d_ctr, c->stream));
+      TW_LAUNCH(c, launch_clear(c->table.ptr, table_bytes, c->d_ctr, c->stream));
       ExpandLaunch a;
       a.kc = kc;
       a.in_keys = static_cast<char*>(c->keys.ptr) + cur.off * w;
@@ -333,15 +342,14 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       if (timed) TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
       const bool table_full = (h.overflow & 2u) || h.out_count * 100ull > slots * 90ull;
       if (table_full) {
-        const double grown = std::max((double)out_cap * 2.0, (double)h.out_count * 1.5);
-        out_cap = (unsigned long long)grown;
-        slots = next_pow2((unsigned long long)std::ceil(grown * 100.0 / load_pct));
+        table_est = std::max(table_est * 2.0, (double)h.out_count * 1.5);
+        out_cap = std::max<unsigned long long>(out_cap, (unsigned long long)std::ceil(table_est));
+        slots = (unsigned long long)std::ceil(table_est * 100.0 / load_pct);
         ++R->retries;
         continue;
       }
       if (h.overflow & 1u) {
         out_cap = h.out_count;  // exact: every insert that won was counted
-        slots = std::max(slots, next_pow2((unsigned long long)std::ceil((double)out_cap * 100.0 / load_pct)));
         ++R->retries;
         continue;
       }

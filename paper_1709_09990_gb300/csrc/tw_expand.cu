@@ -32,6 +32,22 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxComps = 8;
+#ifndef TW_INSERT_UNROLL
+#define TW_INSERT_UNROLL 4  // compare-and-swaps in flight per lane
+#endif
+// Resident warps per SM the register allocation must allow: 32 for the 32-
+// and 64-bit kernels (at most 64 registers per thread, measured fastest on
+// GB300), 16 for the 128-bit kernel.
+template <class K>
+struct ResidentWarps {
+  static constexpr int value = KeyTraits<K>::kBits <= 64 ? 32 : 16;
+};
+
+// Home slot of a hash: the high word of hash * slots (uniform over [0, slots)
+// for any table size, so the table can be sized to the level).
+__device__ __forceinline__ unsigned long long home_slot(unsigned long long h, unsigned long long slots) {
+  return __umul64hi(h, slots);
+}
 
 template <class K>
 struct ExpandParams {
@@ -41,7 +57,7 @@ struct ExpandParams {
   int n;
   int k;
   K* table;
-  unsigned long long table_mask;
+  unsigned long long table_slots;
   int max_probes;
   K* out_keys;
   uint8_t* out_pred;
@@ -98,8 +114,10 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
     if (kpopc(q) > k) continue;
     if (!many) {
 #pragma unroll
-      for (int c = 0; c < kMaxComps; ++c)
+      for (int c = 0; c < kMaxComps; ++c) {
+        if (c >= nc) break;
         if (ktest(comp_b[c], v)) q |= comp_b[c];
+      }
     } else {
       K vis = nv & S;
       K front = vis;
@@ -120,7 +138,8 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
 }
 
 template <class K, int kWarps>
-__global__ void __launch_bounds__(kWarps * 32) expand_insert_kernel(const ExpandParams<K> p) {
+__global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
+    expand_insert_kernel(const ExpandParams<K> p) {
   constexpr int kBits = KeyTraits<K>::kBits;
   __shared__ K sAdj[kBits];
   __shared__ K sState[kWarps][32];
@@ -163,44 +182,84 @@ __global__ void __launch_bounds__(kWarps * 32) expand_insert_kernel(const Expand
     __syncwarp();
     feasible_total += (unsigned long long)total;
 
-    for (int base = 0; base < total; base += 32) {
-      const int j = base + lane;
-      bool won = false;
-      K key = kzero<K>();
-      int v = 0;
-      if (j < total) {
-        const uint16_t e = sQueue[warp][j];
-        v = e & 0xff;
-        key = sState[warp][e >> 8] | kbit<K>(v);
-        unsigned long long h = khash(key) & p.table_mask;
-        for (int probe = 0;; ++probe) {
-          const K old = kcas(&p.table[h], empty, key);
-          if (old == empty) {
-            won = true;
-            break;
-          }
-          if (old == key) break;
-          if (probe + 1 >= p.max_probes) {
-            atomicOr(&p.ctr->overflow, 2u);
-            break;
-          }
-          h = (h + 1ull) & p.table_mask;
+    // Insert the queued pairs, TW_INSERT_UNROLL per lane at a time: the first
+    // probe of every pair is issued before any result is inspected, so each
+    // lane has several compare-and-swaps in flight.
+    constexpr int U = TW_INSERT_UNROLL;
+    for (int base = 0; base < total; base += 32 * U) {
+      K key[U];
+      int vv[U];
+      unsigned long long h[U];
+      int st[U];  // 0 idle, 1 probing, 2 inserted, 3 already present or given up
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = base + u * 32 + lane;
+        st[u] = 0;
+        vv[u] = 0;
+        h[u] = 0;
+        key[u] = kzero<K>();
+        if (j < total) {
+          const uint16_t e = sQueue[warp][j];
+          vv[u] = e & 0xff;
+          key[u] = sState[warp][e >> 8] | kbit<K>(vv[u]);
+          h[u] = home_slot(khash(key[u]), p.table_slots);
+          st[u] = 1;
         }
       }
-      const unsigned wmask = __ballot_sync(kFull, won);
-      if (wmask) {
-        const int leader = __ffs(wmask) - 1;
-        unsigned long long b = 0;
-        if (lane == leader) b = atomicAdd(&p.ctr->out_count, (unsigned long long)__popc(wmask));
-        b = __shfl_sync(kFull, b, leader);
-        if (won) {
-          const unsigned long long o = b + (unsigned long long)__popc(wmask & lanemask_lt);
-          if (o < p.out_cap) {
-            p.out_keys[o] = key;
-            p.out_pred[o] = (uint8_t)v;
-          } else {
-            atomicOr(&p.ctr->overflow, 1u);
+      K old[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (st[u] == 1) old[u] = kcas(&p.table[h[u]], empty, key[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (st[u] != 1) continue;
+        if (old[u] == empty) {
+          st[u] = 2;
+        } else if (old[u] == key[u]) {
+          st[u] = 3;
+        } else {
+          for (int probe = 1;; ++probe) {
+            if (probe >= p.max_probes) {
+              atomicOr(&p.ctr->overflow, 2u);
+              st[u] = 3;
+              break;
+            }
+            h[u] = (h[u] + 1ull == p.table_slots) ? 0ull : h[u] + 1ull;
+            const K o = kcas(&p.table[h[u]], empty, key[u]);
+            if (o == empty) {
+              st[u] = 2;
+              break;
+            }
+            if (o == key[u]) {
+              st[u] = 3;
+              break;
+            }
           }
+        }
+      }
+      unsigned wm[U];
+      int wins = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        wm[u] = __ballot_sync(kFull, st[u] == 2);
+        wins += __popc(wm[u]);
+      }
+      if (wins) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(&p.ctr->out_count, (unsigned long long)wins);
+        b = __shfl_sync(kFull, b, 0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (st[u] == 2) {
+            const unsigned long long o = b + (unsigned long long)__popc(wm[u] & lanemask_lt);
+            if (o < p.out_cap) {
+              p.out_keys[o] = key[u];
+              p.out_pred[o] = (uint8_t)vv[u];
+            } else {
+              atomicOr(&p.ctr->overflow, 1u);
+            }
+          }
+          b += (unsigned long long)__popc(wm[u]);
         }
       }
     }
@@ -218,7 +277,7 @@ cudaError_t launch_expand_t(const ExpandLaunch& a, cudaStream_t s) {
   p.n = a.n;
   p.k = a.k;
   p.table = static_cast<K*>(a.table);
-  p.table_mask = a.table_slots - 1ull;
+  p.table_slots = a.table_slots;
   p.max_probes = a.max_probes;
   p.out_keys = static_cast<K*>(a.out_keys);
   p.out_pred = a.out_pred;
