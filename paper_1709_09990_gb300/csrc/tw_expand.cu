@@ -11,7 +11,7 @@
 //     fill over the adjacency rows held in shared memory; |S| row reads in
 //     total.  Each component C contributes its outer boundary B_C = N(C) \ S.
 //     Then Q(S, v) = (N(v) u U{B_C : v in B_C}) \ (S u {v}), the bitset form
-//     of the depth-first search of Listing 1 (lines 7-19): a vertex outside S
+//     of the depth-first search inside Listing 1: a vertex outside S
 //     is reached from v through S exactly when it borders a component of G[S]
 //     that v borders.  Components with |B_C| >= k+2 make every v in B_C
 //     infeasible at once; up to 8 other boundaries stay in registers, and a
@@ -24,17 +24,15 @@
 //     add per warp.
 #include <cuda_runtime.h>
 
+#include "tw_expand_core.cuh"
 #include "tw_internal.h"
 #include "tw_keys.cuh"
 
 namespace tw {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxComps = 8;
-#ifndef TW_INSERT_UNROLL
-#define TW_INSERT_UNROLL 4  // compare-and-swaps in flight per lane
-#endif
+using core::kFull;
+
 // Resident warps per SM the register allocation must allow: 32 for the 32-
 // and 64-bit kernels (at most 64 registers per thread, measured fastest on
 // GB300), 16 for the 128-bit kernel.
@@ -42,12 +40,6 @@ template <class K>
 struct ResidentWarps {
   static constexpr int value = KeyTraits<K>::kBits <= 64 ? 32 : 16;
 };
-
-// Home slot of a hash: the high word of hash * slots (uniform over [0, slots)
-// for any table size, so the table can be sized to the level).
-__device__ __forceinline__ unsigned long long home_slot(unsigned long long h, unsigned long long slots) {
-  return __umul64hi(h, slots);
-}
 
 template <class K>
 struct ExpandParams {
@@ -65,78 +57,6 @@ struct ExpandParams {
   LevelCounters* ctr;
 };
 
-// The set of vertices v outside S with |Q(S, v)| <= k.
-template <class K>
-__device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict__ sAdj, const K valid,
-                                                 const int k) {
-  K comp_b[kMaxComps];
-#pragma unroll
-  for (int c = 0; c < kMaxComps; ++c) comp_b[c] = kzero<K>();
-  int nc = 0;
-  bool many = false;
-  K dead = kzero<K>();
-  K rem = S;
-  while (!kempty(rem)) {
-    K comp = kzero<K>();
-    K todo = kbit<K>(klowest(rem));
-    K bnd = kzero<K>();
-    while (!kempty(todo)) {
-      const int u = klowest(todo);
-      todo = kdrop_lowest(todo);
-      comp |= kbit<K>(u);
-      const K r = sAdj[u];
-      bnd |= r;
-      todo |= r & rem & ~comp;
-    }
-    rem &= ~comp;
-    bnd &= ~S;
-    const int bs = kpopc(bnd);
-    if (bs >= k + 2) {
-      dead |= bnd;
-    } else if (bs > 0) {
-      if (nc < kMaxComps) {
-#pragma unroll
-        for (int c = 0; c < kMaxComps; ++c)
-          if (c == nc) comp_b[c] = bnd;
-        ++nc;
-      } else {
-        many = true;
-      }
-    }
-  }
-  K cand = valid & ~S & ~dead;
-  K feas = kzero<K>();
-  while (!kempty(cand)) {
-    const int v = klowest(cand);
-    cand = kdrop_lowest(cand);
-    const K nv = sAdj[v];
-    K q = nv & ~S;
-    if (kpopc(q) > k) continue;
-    if (!many) {
-#pragma unroll
-      for (int c = 0; c < kMaxComps; ++c) {
-        if (c >= nc) break;
-        if (ktest(comp_b[c], v)) q |= comp_b[c];
-      }
-    } else {
-      K vis = nv & S;
-      K front = vis;
-      while (!kempty(front)) {
-        const int u = klowest(front);
-        front = kdrop_lowest(front);
-        const K r = sAdj[u];
-        q |= r & ~S;
-        const K nw = r & S & ~vis;
-        vis |= nw;
-        front |= nw;
-      }
-    }
-    q &= ~kbit<K>(v);
-    if (kpopc(q) <= k) feas |= kbit<K>(v);
-  }
-  return feas;
-}
-
 template <class K, int kWarps>
 __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
     expand_insert_kernel(const ExpandParams<K> p) {
@@ -150,119 +70,28 @@ __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const unsigned lanemask_lt = (1u << lane) - 1u;
   const K valid = kfirst_n<K>(p.n);
-  const K empty = kones<K>();
   unsigned long long feasible_total = 0;
   const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
   const unsigned long long stride = (unsigned long long)gridDim.x * kWarps;
+  core::LevelOut<K, false> out;
+  out.keys = p.out_keys;
+  out.pred = p.out_pred;
+  out.parent = nullptr;
+  out.parent_base = 0;
+  out.cap = p.out_cap;
+  out.count = &p.ctr->out_count;
+  out.overflow = &p.ctr->overflow;
 
   for (unsigned long long chunk = (unsigned long long)blockIdx.x * kWarps + warp; chunk < n_chunks;
        chunk += stride) {
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;
     const K S = active ? p.in_keys[idx] : valid;
-    K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.k) : kzero<K>();
-
-    const int cnt = kpopc(feas);
-    int incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int t = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl += t;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    int pos = incl - cnt;
-    sState[warp][lane] = S;
-    while (!kempty(feas)) {
-      const int v = klowest(feas);
-      feas = kdrop_lowest(feas);
-      sQueue[warp][pos++] = (uint16_t)((lane << 8) | v);
-    }
-    __syncwarp();
+    const K feas = active ? core::feasible_extensions<K>(S, sAdj, valid, p.k) : kzero<K>();
+    const int total = core::build_queue<K>(S, feas, lane, sState[warp], sQueue[warp]);
     feasible_total += (unsigned long long)total;
-
-    // Insert the queued pairs, TW_INSERT_UNROLL per lane at a time: the first
-    // probe of every pair is issued before any result is inspected, so each
-    // lane has several compare-and-swaps in flight.
-    constexpr int U = TW_INSERT_UNROLL;
-    for (int base = 0; base < total; base += 32 * U) {
-      K key[U];
-      int vv[U];
-      unsigned long long h[U];
-      int st[U];  // 0 idle, 1 probing, 2 inserted, 3 already present or given up
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int j = base + u * 32 + lane;
-        st[u] = 0;
-        vv[u] = 0;
-        h[u] = 0;
-        key[u] = kzero<K>();
-        if (j < total) {
-          const uint16_t e = sQueue[warp][j];
-          vv[u] = e & 0xff;
-          key[u] = sState[warp][e >> 8] | kbit<K>(vv[u]);
-          h[u] = home_slot(khash(key[u]), p.table_slots);
-          st[u] = 1;
-        }
-      }
-      K old[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (st[u] == 1) old[u] = kcas(&p.table[h[u]], empty, key[u]);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (st[u] != 1) continue;
-        if (old[u] == empty) {
-          st[u] = 2;
-        } else if (old[u] == key[u]) {
-          st[u] = 3;
-        } else {
-          for (int probe = 1;; ++probe) {
-            if (probe >= p.max_probes) {
-              atomicOr(&p.ctr->overflow, 2u);
-              st[u] = 3;
-              break;
-            }
-            h[u] = (h[u] + 1ull == p.table_slots) ? 0ull : h[u] + 1ull;
-            const K o = kcas(&p.table[h[u]], empty, key[u]);
-            if (o == empty) {
-              st[u] = 2;
-              break;
-            }
-            if (o == key[u]) {
-              st[u] = 3;
-              break;
-            }
-          }
-        }
-      }
-      unsigned wm[U];
-      int wins = 0;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        wm[u] = __ballot_sync(kFull, st[u] == 2);
-        wins += __popc(wm[u]);
-      }
-      if (wins) {
-        unsigned long long b = 0;
-        if (lane == 0) b = atomicAdd(&p.ctr->out_count, (unsigned long long)wins);
-        b = __shfl_sync(kFull, b, 0);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (st[u] == 2) {
-            const unsigned long long o = b + (unsigned long long)__popc(wm[u] & lanemask_lt);
-            if (o < p.out_cap) {
-              p.out_keys[o] = key[u];
-              p.out_pred[o] = (uint8_t)vv[u];
-            } else {
-              atomicOr(&p.ctr->overflow, 1u);
-            }
-          }
-          b += (unsigned long long)__popc(wm[u]);
-        }
-      }
-    }
+    core::insert_queue<K, false>(sQueue[warp], sState[warp], total, lane, p.table, p.table_slots, p.max_probes, out);
     __syncwarp();
   }
   if (lane == 0 && feasible_total) atomicAdd(&p.ctr->feasible, feasible_total);

@@ -1,0 +1,248 @@
+// Device building blocks of one wavefront level, shared by the single-graph
+// and the batched expansion kernels.
+//
+// Level i -> i+1 of Listing 1 (arXiv 1709.09990, Section 3.1): every set S of
+// L_i is extended by every vertex v outside S with |Q(S, v)| <= k, and the
+// extensions are deduplicated (Section 3.2) in an exact hash table.
+#pragma once
+
+#include <cstdint>
+
+#include "tw_internal.h"
+#include "tw_keys.cuh"
+
+namespace tw {
+namespace core {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxComps = 8;
+#ifndef TW_INSERT_UNROLL
+#define TW_INSERT_UNROLL 4  // compare-and-swaps in flight per lane
+#endif
+
+// Home slot of a hash: the high word of hash * slots (uniform over [0, slots)
+// for any table size, so the table can be sized to the level).
+__device__ __forceinline__ unsigned long long home_slot(unsigned long long h, unsigned long long slots) {
+  return __umul64hi(h, slots);
+}
+
+// The set of vertices v outside S with |Q(S, v)| <= k (thread per state).
+//
+// The components of G[S] are found by a bitset flood fill over the adjacency
+// rows in shared memory (|S| row reads in total); each component C gives its
+// outer boundary B_C = N(C) \ S.  A vertex outside S is reachable from v
+// through S exactly when it borders a component that v borders, so
+// Q(S, v) = (N(v) u U{B_C : v in B_C}) \ (S u {v}) - the bitset form of the
+// search of Listing 1.  A boundary with |B_C| >= k+2 rules out all of B_C at
+// once; up to kMaxComps other boundaries stay in registers, and a state with
+// more falls back to a flood fill per candidate.
+template <class K>
+__device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict__ sAdj, const K valid,
+                                                 const int k) {
+  K comp_b[kMaxComps];
+#pragma unroll
+  for (int c = 0; c < kMaxComps; ++c) comp_b[c] = kzero<K>();
+  int nc = 0;
+  bool many = false;
+  K dead = kzero<K>();
+  K rem = S;
+  while (!kempty(rem)) {
+    K comp = kzero<K>();
+    K todo = kbit<K>(klowest(rem));
+    K bnd = kzero<K>();
+    while (!kempty(todo)) {
+      const int u = klowest(todo);
+      todo = kdrop_lowest(todo);
+      comp |= kbit<K>(u);
+      const K r = sAdj[u];
+      bnd |= r;
+      todo |= r & rem & ~comp;
+    }
+    rem &= ~comp;
+    bnd &= ~S;
+    const int bs = kpopc(bnd);
+    if (bs >= k + 2) {
+      dead |= bnd;
+    } else if (bs > 0) {
+      if (nc < kMaxComps) {
+#pragma unroll
+        for (int c = 0; c < kMaxComps; ++c)
+          if (c == nc) comp_b[c] = bnd;
+        ++nc;
+      } else {
+        many = true;
+      }
+    }
+  }
+  K cand = valid & ~S & ~dead;
+  K feas = kzero<K>();
+  while (!kempty(cand)) {
+    const int v = klowest(cand);
+    cand = kdrop_lowest(cand);
+    const K nv = sAdj[v];
+    K q = nv & ~S;
+    if (kpopc(q) > k) continue;
+    if (!many) {
+#pragma unroll
+      for (int c = 0; c < kMaxComps; ++c) {
+        if (c >= nc) break;
+        if (ktest(comp_b[c], v)) q |= comp_b[c];
+      }
+    } else {
+      K vis = nv & S;
+      K front = vis;
+      while (!kempty(front)) {
+        const int u = klowest(front);
+        front = kdrop_lowest(front);
+        const K r = sAdj[u];
+        q |= r & ~S;
+        const K nw = r & S & ~vis;
+        vis |= nw;
+        front |= nw;
+      }
+    }
+    q &= ~kbit<K>(v);
+    if (kpopc(q) <= k) feas |= kbit<K>(v);
+  }
+  return feas;
+}
+
+// Packs the feasible (S, v) pairs of the warp's 32 states into the warp's
+// queue (entry = lane << 8 | v) and stores each lane's S; returns the number
+// of pairs (warp uniform).
+template <class K>
+__device__ __forceinline__ int build_queue(const K S, K feas, const int lane, K* __restrict__ sS,
+                                           uint16_t* __restrict__ sQ) {
+  const int cnt = kpopc(feas);
+  int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += t;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  int pos = incl - cnt;
+  sS[lane] = S;
+  while (!kempty(feas)) {
+    const int v = klowest(feas);
+    feas = kdrop_lowest(feas);
+    sQ[pos++] = (uint16_t)((lane << 8) | v);
+  }
+  __syncwarp();
+  return total;
+}
+
+// Where the winners of the inserts go.  With kParent the output records the
+// index (parent_base + lane) of the parent state in its level; otherwise the
+// added vertex.
+template <class K, bool kParent>
+struct LevelOut {
+  K* keys;
+  uint8_t* pred;       // used when !kParent
+  uint32_t* parent;    // used when kParent
+  uint32_t parent_base;
+  unsigned long long cap;
+  unsigned long long* count;
+  unsigned int* overflow;  // bit 0: output full, bit 1: probe limit
+};
+
+// Inserts the queued pairs into the table, TW_INSERT_UNROLL per lane at a
+// time: the first probe of every pair is issued before any result is
+// inspected, so each lane has several compare-and-swaps in flight.  Linear
+// probing from the home slot, at most max_probes slots.  Winners append
+// (S u {v}, pred or parent) with one atomic add per round of the warp.
+template <class K, bool kParent>
+__device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, const K* __restrict__ sS,
+                                             const int total, const int lane, K* __restrict__ table,
+                                             const unsigned long long slots, const int max_probes,
+                                             const LevelOut<K, kParent>& out) {
+  constexpr int U = TW_INSERT_UNROLL;
+  const K empty = kones<K>();
+  const unsigned lanemask_lt = (1u << lane) - 1u;
+  for (int base = 0; base < total; base += 32 * U) {
+    K key[U];
+    int vv[U];
+    int src[U];
+    unsigned long long h[U];
+    int st[U];  // 0 idle, 1 probing, 2 inserted, 3 already present or given up
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = base + u * 32 + lane;
+      st[u] = 0;
+      vv[u] = 0;
+      src[u] = 0;
+      h[u] = 0;
+      key[u] = kzero<K>();
+      if (j < total) {
+        const uint16_t e = sQ[j];
+        vv[u] = e & 0xff;
+        src[u] = e >> 8;
+        key[u] = sS[src[u]] | kbit<K>(vv[u]);
+        h[u] = home_slot(khash(key[u]), slots);
+        st[u] = 1;
+      }
+    }
+    K old[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (st[u] == 1) old[u] = kcas(&table[h[u]], empty, key[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (st[u] != 1) continue;
+      if (old[u] == empty) {
+        st[u] = 2;
+      } else if (old[u] == key[u]) {
+        st[u] = 3;
+      } else {
+        for (int probe = 1;; ++probe) {
+          if (probe >= max_probes) {
+            atomicOr(out.overflow, 2u);
+            st[u] = 3;
+            break;
+          }
+          h[u] = (h[u] + 1ull == slots) ? 0ull : h[u] + 1ull;
+          const K o = kcas(&table[h[u]], empty, key[u]);
+          if (o == empty) {
+            st[u] = 2;
+            break;
+          }
+          if (o == key[u]) {
+            st[u] = 3;
+            break;
+          }
+        }
+      }
+    }
+    unsigned wm[U];
+    int wins = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      wm[u] = __ballot_sync(kFull, st[u] == 2);
+      wins += __popc(wm[u]);
+    }
+    if (wins) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(out.count, (unsigned long long)wins);
+      b = __shfl_sync(kFull, b, 0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (st[u] == 2) {
+          const unsigned long long o = b + (unsigned long long)__popc(wm[u] & lanemask_lt);
+          if (o < out.cap) {
+            out.keys[o] = key[u];
+            if (kParent)
+              out.parent[o] = out.parent_base + (uint32_t)src[u];
+            else
+              out.pred[o] = (uint8_t)vv[u];
+          } else {
+            atomicOr(out.overflow, 1u);
+          }
+        }
+        b += (unsigned long long)__popc(wm[u]);
+      }
+    }
+  }
+}
+
+}  // namespace core
+}  // namespace tw

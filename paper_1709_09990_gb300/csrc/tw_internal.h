@@ -79,6 +79,55 @@ cudaError_t launch_td(const unsigned long long* adj64, int n, int words64, const
 cudaError_t launch_bounds(const unsigned long long* adj, const int32_t* n, const int64_t* row_offset,
                           int num_graphs, int32_t* out, float* feats, cudaStream_t s);
 
+// ---- batched expansion (tw_batch.cu) ---------------------------------------
+// One graph's share of a batched level step (64-bit states, n <= 64).
+struct BatchSeg {
+  unsigned long long in_off;    // arena index of the graph's L_i
+  unsigned long long in_count;  // |L_i|
+  unsigned long long t_off;     // first slot of the graph's table segment
+  unsigned long long t_slots;   // slots of that segment
+  unsigned long long o_off;     // first entry of the graph's output segment
+  unsigned long long o_cap;     // capacity of that segment
+  int graph;                    // row block of the graph in the adjacency array (64 rows each)
+  int n;
+  int k;
+  int pad;
+};
+
+struct BatchCounters {
+  unsigned long long out_count;
+  unsigned long long feasible;
+  unsigned int overflow;  // bit 0: output full, bit 1: probe limit
+  unsigned int pad;
+  unsigned long long pad2;
+};
+
+struct CopySeg {
+  unsigned long long src_off;  // ~0 = write the empty set
+  unsigned long long dst_off;
+  unsigned long long count;
+};
+
+struct WalkSeg {
+  unsigned long long level_base;  // index of the graph's level offsets in level_off
+  unsigned long long order_off;   // first entry of the graph's ordering
+  int last;                       // index of the final level
+  int n;
+};
+
+// chunk_begin has nseg+1 entries (the last one = total_chunks); segments
+// must be non-empty.  Keys are u64, parents u32.
+cudaError_t launch_expand_batch(const BatchSeg* segs, const unsigned long long* chunk_begin, int nseg,
+                                unsigned long long total_chunks, const unsigned long long* keys,
+                                const unsigned long long* adj_all, unsigned long long* table,
+                                unsigned long long* out_keys, uint32_t* out_parent, BatchCounters* ctr, int max_probes,
+                                cudaStream_t s);
+cudaError_t launch_copy_segments(const CopySeg* segs, int nseg, const unsigned long long* src_keys,
+                                 const uint32_t* src_par, unsigned long long* dst_keys, uint32_t* dst_par,
+                                 cudaStream_t s);
+cudaError_t launch_walk_batch(const WalkSeg* walks, int nwalk, const unsigned long long* level_off,
+                              const unsigned long long* keys, const uint32_t* par, int32_t* orders, cudaStream_t s);
+
 // Network kernels.
 cudaError_t launch_mlp_forward(const float* params, const float* x, int batch, float* yhat, cudaStream_t s);
 cudaError_t launch_mlp_grad(const float* params, const float* x, const float* y, int batch,

@@ -140,3 +140,33 @@ def test_batch_with_hints_is_exact(ctx):
         res = ctx.solve_batch(graphs, k_hint=hint)
         assert res["status"] == 0
         assert res["tw"].tolist() == exact
+
+
+def test_batched_path_mixed_sizes_and_hints(ctx):
+    # graphs of 10..64 vertices go through the batched kernel, larger ones
+    # through the single-graph path; tw must equal the oracle's for all
+    graphs = [gg.mixed_graph(900 + j, 10, 26, j % 2 == 0) for j in range(60)]
+    graphs += [gg.gnp(60, 0.7, 12), gg.gnp(70, 0.8, 110), gg.complete(5), [0], gg.path(33)]
+    exact = []
+    for a in graphs:
+        lb = max(obounds.mmd(a), obounds.mmd_plus(a))
+        exact.append(oracle.solve(a, k_start=lb, want_order=False)["tw"])
+    for hint in (None, np.array(exact, np.float32) + 2, np.array(exact, np.float32) - 2):
+        res = ctx.solve_batch(graphs, k_hint=hint)
+        assert res["status"] == 0
+        assert res["tw"].tolist() == exact
+        pos = 0
+        for g, adj in enumerate(graphs):
+            order = res["orders"][pos: pos + len(adj)].tolist()
+            assert oracle.width_q(adj, order) == exact[g]
+            pos += len(adj)
+
+
+def test_batched_path_evicts_large_levels(ctx):
+    # the geometric n=40 graph has levels of ~5.9 M states: it leaves the
+    # batch and is finished by the single-graph path
+    graphs = [gg.workload_gnp20(), gg.workload_rgg40(), gg.cycle(12)]
+    res = ctx.solve_batch(graphs)
+    assert res["status"] == 0
+    assert res["tw"].tolist() == [8, 6, 2]
+    assert res["stats"]["states_expanded"] >= 79399414
