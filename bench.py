@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample length for cpu_baseline")
+    ap.add_argument("--workload", default="rgg40", choices=["rgg40", "gnp20", "pktree60", "batch", "learned"],
+                    help="rgg40 (default): the n=40 geometric graph; gnp20: G(20,0.3); pktree60: the partial "
+                         "10-tree n=60 at k=10; batch: the 4096-graph batch vs a per-graph loop; learned: the "
+                         "learned starting bound vs the plain sweep")
+    ap.add_argument("--graphs", type=int, default=0, help="batch/learned: number of graphs (0 = full workload)")
+    ap.add_argument("--mem-cap-gb", type=float, default=0.0, help="device memory cap per context (0 = default)")
     return ap.parse_args()
 
 
@@ -297,12 +303,179 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------ other workloads
+def _line(metric, value, unit, args, config, extra):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": unit.endswith("/s"), "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic", "config": config}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def run_gnp20(args):
+    """G(20, 0.3) seed 0, 32-bit states: the sweep from the lower bound (k = 6,
+    7, 8) with ordering and tree decomposition; launch-latency bound."""
+    import numpy as np
+    import torch
+    from paper_1709_09990_gb300 import graphgen as gg
+    from paper_1709_09990_gb300 import native
+    adj = gg.workload_gnp20()
+    stream = torch.cuda.Stream()
+    ctx = native.Context(device=0, stream=stream.cuda_stream, time_kernels=True)
+    rows = torch.from_numpy(gg.to_rows_u64(adj).astype(np.int64)).cuda()
+    for _ in range(args.warmup):
+        ctx.solve(rows, n=20, want_td=True)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(stream)
+        res = ctx.solve(rows, n=20, want_td=True)
+        b.record(stream)
+    torch.cuda.synchronize()
+    dt = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    st = res["stats"]
+    _line(METRIC, round(st["states_expanded"] * args.steps / dt, 1), UNIT, args,
+          {"workload": "G(n=20, p=0.3) seed 0; plain sweep from the lower bound to exact tw", "n": 20, "tw": res["tw"],
+           "states_per_step": st["states_expanded"], "decide_runs_per_step": st["decide_runs"],
+           "level_sizes_final_k": st["level_size"]},
+          {"ms_per_step": round(1e3 * dt / args.steps, 4), "time_to_exact_tw_ms": round(1e3 * dt / args.steps, 4),
+           "gpu_launches": st["kernel_launches"] * args.steps, "dtype": "u32"})
+    ctx.close()
+
+
+def run_pktree60(args):
+    """Partial 10-tree n=60 seed 0: decide at k = 10 (the lower bound, equal to
+    the heuristic width) under the memory cap; the run ends with the capacity
+    status when a level does not fit, and the levels reached are reported."""
+    from paper_1709_09990_gb300 import graphgen as gg
+    from paper_1709_09990_gb300 import native
+    adj = gg.workload_pktree60()
+    cap = int(args.mem_cap_gb * (1 << 30))
+    with native.Context(device=0, mem_cap_bytes=cap, time_kernels=True) as ctx:
+        b = ctx.bounds(adj).tolist()
+        t = time.perf_counter()
+        r = ctx.decide(adj, k=10, raise_on_error=False)
+        dt = time.perf_counter() - t
+    st = r["stats"]
+    _line(METRIC, round(st["states_expanded"] / dt, 1), UNIT, args,
+          {"workload": "partial 10-tree n=60 (30% of edges removed) seed 0; decide at k=10", "n": 60,
+           "bounds": {"mmd": b[0], "mmd_plus": b[1], "min_degree_width": b[2], "min_fill_width": b[3]},
+           "mem_cap_gb": args.mem_cap_gb or "default"},
+          {"status": native.strerror(r["status"]), "status_code": r["status"], "seconds": round(dt, 3),
+           "levels_reached": st["level_size"], "states_expanded": st["states_expanded"],
+           "peak_frontier_bytes": st["peak_frontier_bytes"],
+           "tw_certified_by_bounds": b[1] if max(b[0], b[1]) == min(b[2], b[3]) else None,
+           "expand_algorithmic_GBps": round(st["expand_bytes"] / st["expand_seconds"] / 1e9, 1)
+           if st["expand_seconds"] else None})
+
+
+def run_batch(args):
+    """The 4096-graph batch (G(n,p) and partial k-trees, n in [16, 48]) through
+    tw_solve_batch against a per-graph tw_solve loop on the same GPU."""
+    import numpy as np
+    from paper_1709_09990_gb300 import graphgen as gg
+    from paper_1709_09990_gb300 import native
+    N = args.graphs or 4096
+    graphs = gg.batch_graphs(N)
+    cap = int((args.mem_cap_gb or 16) * (1 << 30))
+    with native.Context(device=0, mem_cap_bytes=cap) as ctx:
+        ctx.solve_batch(graphs[:16])
+        t = time.perf_counter()
+        res = ctx.solve_batch(graphs)
+        tb = time.perf_counter() - t
+        loop_tw, loop_st, loop_states = [], [], 0
+        t = time.perf_counter()
+        for a in graphs:
+            try:
+                r = ctx.solve(a, want_order=True)
+                loop_tw.append(r["tw"])
+                loop_st.append(0)
+                loop_states += r["stats"]["states_expanded"]
+            except native.TwError as e:
+                loop_tw.append(-1)
+                loop_st.append(e.status)
+        tl = time.perf_counter() - t
+    ok = res["per_graph_status"] == 0
+    agree = all(a == b for a, b in zip(res["tw"].tolist(), loop_tw))
+    st = res["stats"]
+    _line("time to exact tw, batch", round(tb, 3), "s", args,
+          {"workload": f"{N} seeded graphs: even seeds G(n,p), n~U{{16..48}}, p~U[0.1,0.5]; odd seeds partial "
+                       "k-trees, k~U{3..12}, 30% edges removed", "graphs": N,
+           "mem_cap_gb": cap / (1 << 30)},
+          {"solved": int(ok.sum()), "capacity": int((res["per_graph_status"] == 2).sum()),
+           "batch_states_per_s": round(st["states_expanded"] / tb, 1), "loop_seconds": round(tl, 3),
+           "loop_states_per_s": round(loop_states / tl, 1), "speedup_vs_loop": round(tl / tb, 3),
+           "same_answers_as_loop": bool(agree), "kernel_launches_batch": st["kernel_launches"]})
+
+
+def run_learned(args):
+    """Learned starting bound: label and train on the 20000 training graphs
+    (n in [12, 40]), then solve the 2000 held-out graphs (n in [30, 56]) with
+    proposals (batched) and with the plain per-graph sweep."""
+    import numpy as np
+    from paper_1709_09990_gb300 import graphgen as gg
+    from paper_1709_09990_gb300 import learned
+    from paper_1709_09990_gb300 import native
+    ntr = args.graphs * 10 if args.graphs else 20000
+    nte = args.graphs or 2000
+    cap = int((args.mem_cap_gb or 8) * (1 << 30))
+    tr = [gg.mixed_graph(10**6 + j, 12, 40, j % 2 == 0) for j in range(ntr)]
+    te = [gg.mixed_graph(2 * 10**6 + j, 30, 56, j % 2 == 0) for j in range(nte)]
+    with native.Context(device=0, mem_cap_bytes=cap) as ctx:
+        L = learned.label(ctx, tr)
+        ok = L["status"] == 0
+        # offset chosen on a validation split of the training graphs
+        idx = np.arange(len(tr))[ok]
+        val = idx[idx % 10 == 0]
+        fit = idx[idx % 10 != 0]
+        t = time.perf_counter()
+        T = learned.train(ctx, L["x"][fit], L["tw"][fit], L["n"][fit], epochs=60)
+        train_s = time.perf_counter() - t
+        lbv = np.array([max(ctx.bounds(tr[i])[:2]) for i in val])
+        pv = learned.propose(ctx, T["params"], L["x"][val], L["n"][val])
+        off = learned.choose_offset(pv, L["tw"][val], lbv)
+        n = np.array([len(g) for g in te], np.int32)
+        t = time.perf_counter()
+        hint = learned.propose(ctx, T["params"], ctx.features(te), n, off)
+        lk = ctx.solve_batch(te, k_hint=hint)
+        t_learned = time.perf_counter() - t
+        t = time.perf_counter()
+        pb = ctx.solve_batch(te)
+        t_plain_batch = time.perf_counter() - t
+        loop_tw, runs = [], 0
+        t = time.perf_counter()
+        for g in te:
+            try:
+                r = ctx.solve(g, want_order=True)
+                loop_tw.append(r["tw"])
+                runs += r["stats"]["decide_runs"]
+            except native.TwError:
+                loop_tw.append(-1)
+        t_loop = time.perf_counter() - t
+    okl = lk["per_graph_status"] == 0
+    loop_tw = np.array(loop_tw)
+    both = okl & (loop_tw >= 0)
+    _line("time to exact tw, learned-k batched", round(t_learned, 3), "s", args,
+          {"workload": f"train {ntr} graphs n in [12,40] (seeds 1e6+j), test {nte} graphs n in [30,56] "
+                       "(seeds 2e6+j), mixed G(n,p) / partial k-trees", "mem_cap_gb": cap / (1 << 30)},
+          {"label_seconds": round(L["seconds"], 2), "train_seconds": round(train_s, 3),
+           "train_graphs_used": int(ok.sum()), "final_train_loss": float(T["loss"][-1]), "offset": off,
+           "test_solved": int(okl.sum()), "test_capacity": int((lk["per_graph_status"] == 2).sum()),
+           "exact_answer_rate": float((lk["tw"][both] == loop_tw[both]).mean()) if both.any() else None,
+           "proposal_hits_tw": float((np.rint(hint[both]) == loop_tw[both]).mean()) if both.any() else None,
+           "plain_loop_seconds": round(t_loop, 3), "plain_batch_seconds": round(t_plain_batch, 3),
+           "speedup_vs_plain_loop": round(t_loop / t_learned, 3),
+           "decide_runs": {"learned_batch": lk["stats"]["decide_runs"], "plain_loop": runs}})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "rgg40":
         run_ours(args)
+    else:
+        {"gnp20": run_gnp20, "pktree60": run_pktree60, "batch": run_batch, "learned": run_learned}[args.workload](args)
 
 
 if __name__ == "__main__":
