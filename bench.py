@@ -108,6 +108,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------- multi-rank
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, slowest_seconds: float) -> float:
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / slowest_seconds
+
+
 # ------------------------------------------------------------ CPU baseline
 def oracle_sample(seconds: float):
     """The CPU oracle as it stands on a bounded sample of the workload: the
@@ -198,15 +215,12 @@ def run_ours(args):
         stats.append(res["stats"])
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    dev_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dev)
     if world > 1:
-        t = torch.tensor([dev_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
         dist.barrier()
     tw = int(tw_dev.item())
     states_step = stats[-1]["states_expanded"]
-    value = states_step * args.steps * world / dev_s
+    value = job_throughput(states_step * args.steps, world, dev_s)
 
     # end to end through the C ABI with host buffers (pinned)
     rows_pin = torch.from_numpy(rows_host).pin_memory()
@@ -225,10 +239,7 @@ def run_ours(args):
         native.lib().tw_solve(ctx._h, rows_pin.data_ptr(), n, tw_pin.data_ptr(), order_pin.data_ptr(),
                               parent_pin.data_ptr(), None, None)
         e2e_s += time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dev)
     assert int(tw_pin[0]) == tw
 
     st = stats[-1]
@@ -253,7 +264,7 @@ def run_ours(args):
                       "peak_frontier_bytes": st["peak_frontier_bytes"], "l2": "flushed (512 MiB write) before each step",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "time_to_exact_tw_ms": round(1e3 * dev_s / args.steps, 3),
-           "e2e": {"value": round(states_step * args.steps * world / e2e_s, 1), "unit": UNIT,
+           "e2e": {"value": round(job_throughput(states_step * args.steps, world, e2e_s), 1), "unit": UNIT,
                    "h2d_bytes_per_step": int(rows_host.nbytes), "d2h_bytes_per_step": 4 + 8 * n,
                    "ms_per_step": round(1e3 * e2e_s / args.steps, 3)},
            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),

@@ -49,11 +49,8 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+def _bind(lib):
+    """Declares the C signatures on a loaded oracle library."""
     lib.orc_set_fingerprint.restype = ctypes.c_uint64
     lib.orc_set_fingerprint.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
     lib.orc_valid_graph.argtypes = [_u64p, ctypes.c_int]
@@ -67,8 +64,14 @@ def _load():
     lib.orc_subset_dp.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, _i64p, _u64p, _u64p, _intp]
     lib.orc_td_from_order.argtypes = [_u64p, ctypes.c_int, _i32p, _i32p, _u64p]
     lib.orc_verify_td.argtypes = [_u64p, ctypes.c_int, _i32p, _u64p]
-    _lib = lib
     return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(build()))
+    return _lib
 
 
 def _ptr(a: np.ndarray, t):

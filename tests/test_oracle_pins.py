@@ -163,6 +163,12 @@ def test_tw_invariant_under_relabelling():
         assert oracle.solve(adj)["tw"] == oracle.solve(gg.relabel(adj, s))["tw"]
 
 
+def test_fingerprint_is_splitmix64_output():
+    # the first output of splitmix64 from seed 0 (Steele, Lea & Flood 2014)
+    # is the output function applied to the golden-ratio increment
+    assert oracle.fingerprint(0x9E3779B97F4A7C15) == 0xE220A8397B1DCDAF
+
+
 def test_fingerprint_distinguishes_words():
     assert oracle.fingerprint(1) != oracle.fingerprint(1 << 64)
     assert oracle.fingerprint(0) == 0
