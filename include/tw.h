@@ -64,7 +64,11 @@ typedef struct {
   int max_probes;         /* probe limit per insert; 0 = default (cap of table)  */
   int ub_shortcut;        /* tw_solve: accept the heuristic upper bound when the
                              lower bound meets it, without a decide run (0 = off) */
-  int graph_levels;       /* 1 = drive levels through a captured CUDA graph       */
+  int graph_levels;       /* 1: run each decide's level loop as one captured CUDA
+                             graph when the context's buffers can hold it (else
+                             the host loop); -1: host-driven loop, one host round
+                             trip per level; 0: the library default.  time_kernels
+                             forces the host loop.                               */
   int time_kernels;       /* 1 = time every expand launch with CUDA events on the
                              context's stream (fills expand_seconds)              */
   int reserved[6];        /* must be zero                                         */

@@ -50,6 +50,17 @@ struct tw_ctx {
   int sms = 0;
   unsigned long long launches = 0;       // libtw kernels launched so far
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // expand timing (time_kernels)
+  // graph-driven level loops, instantiated once per shape and buffer set
+  struct GraphEntry {
+    int kc, n, k, load, probes, bt;
+    void *keys, *pred, *table;
+    unsigned long long arena_cap, table_cap;
+    cudaGraphExec_t exec;
+    int nodes;
+  };
+  std::vector<GraphEntry> graphs;
+  GraphState* d_gstate = nullptr;
+  GraphState* h_gstate = nullptr;
 };
 
 namespace {
@@ -381,6 +392,134 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
   return TW_OK;
 }
 
+// decide(k) with the level loop as one captured CUDA graph (every level kept).
+// *bailed is set when the graph gave up (a level did not fit the current
+// buffers or its estimate); the caller then runs the host loop.
+int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool* bailed) {
+  *bailed = true;
+  const int w = (int)key_bytes(kc);
+  if (k >= n - 1) return TW_OK;
+  const unsigned long long arena_cap = std::min<unsigned long long>(c->keys.bytes / w, c->pred.bytes);
+  const unsigned long long table_cap = c->table.bytes >= 16 ? (c->table.bytes - 16) / w : 0;
+  if (arena_cap < 64 || table_cap < 64) return TW_OK;
+  const int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
+  tw_ctx::GraphEntry* e = nullptr;
+  for (auto& g : c->graphs)
+    if (g.kc == (int)kc && g.n == n && g.k == k && g.load == load_pct && g.probes == max_probes &&
+        g.bt == c->cfg.block_threads && g.keys == c->keys.ptr && g.pred == c->pred.ptr && g.table == c->table.ptr &&
+        g.arena_cap == arena_cap && g.table_cap == table_cap)
+      e = &g;
+  if (e == nullptr) {
+    if (c->graphs.size() >= 32) {
+      TW_CK(cudaStreamSynchronize(c->stream));
+      for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+      c->graphs.clear();
+    }
+    SmallLayout L;
+    ExpandLaunch a;
+    a.kc = kc;
+    a.in_keys = c->keys.ptr;
+    a.n_in = 0;
+    a.adj = small_at(c, L.adj);
+    a.n = n;
+    a.k = k;
+    a.table = c->table.ptr;
+    a.table_slots = 0;
+    a.max_probes = max_probes;
+    a.out_keys = c->keys.ptr;
+    a.out_pred = static_cast<uint8_t*>(c->pred.ptr);
+    a.out_cap = 0;
+    a.ctr = c->d_ctr;
+    a.block_threads = 128;
+    a.grid = 0;
+    cudaGraph_t graph = nullptr;
+    TW_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    int nodes = 0;
+    cudaError_t err = launch_graph_init(kc, c->d_gstate, c->keys.ptr, c->stream);
+    ++nodes;
+    if (err == cudaSuccess)
+      err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, n, k, load_pct, w, 1, c->stream);
+    ++nodes;
+    for (int i = 0; i <= n - k - 2 && err == cudaSuccess; ++i) {
+      err = launch_graph_clear(kc, c->d_gstate, c->table.ptr, c->stream);
+      if (err == cudaSuccess) err = launch_graph_expand(c->d_gstate, a, c->stream);
+      if (err == cudaSuccess)
+        err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, n, k, load_pct, w, 0, c->stream);
+      nodes += 3;
+    }
+    const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
+    if (err != cudaSuccess || end != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return TW_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t inst = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TW_CK(inst);
+    c->graphs.push_back({(int)kc, n, k, load_pct, max_probes, c->cfg.block_threads, c->keys.ptr, c->pred.ptr,
+                         c->table.ptr, arena_cap, table_cap, exec, nodes});
+    e = &c->graphs.back();
+  }
+  TW_CK(cudaGraphLaunch(e->exec, c->stream));
+  c->launches += (unsigned long long)e->nodes;
+  TW_CK(cudaMemcpyAsync(c->h_gstate, c->d_gstate, sizeof(GraphState), cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaStreamSynchronize(c->stream));
+  const GraphState& h = *c->h_gstate;
+  if (h.bail || !h.done) return TW_OK;
+  *bailed = false;
+  R->levels.clear();
+  R->fp_sum.assign(1, 0ull);
+  R->fp_xor.assign(1, 0ull);
+  R->states_expanded = R->candidates = R->retries = 0;
+  R->expand_launches = 0;
+  R->expand_seconds = R->expand_bytes = 0.0;
+  for (int j = 0; j <= h.cur; ++j) R->levels.push_back({h.level_off[j], h.level_cnt[j]});
+  for (int j = 0; j < h.cur; ++j) {
+    R->states_expanded += h.level_cnt[j];
+    R->candidates += h.level_cnt[j] * (unsigned long long)(n - j);
+    R->expand_bytes += (double)(h.level_cnt[j] + 2ull * h.level_cnt[j + 1]) * (double)w + (double)h.level_cnt[j + 1];
+  }
+  R->feasible = h.feasible;
+  R->expand_bytes += (double)h.feasible * (double)w;
+  R->expand_launches = (unsigned long long)h.cur;
+  R->peak_bytes = h.peak_bytes;
+  R->yes = h.yes;
+  if (c->cfg.fingerprints) {
+    for (int j = 1; j <= h.cur; ++j) {
+      TW_CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(LevelCounters), c->stream));
+      TW_LAUNCH(c, launch_fingerprint(kc, static_cast<char*>(c->keys.ptr) + h.level_off[j] * w, h.level_cnt[j],
+                                      c->d_ctr, c->stream));
+      TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      R->fp_sum.push_back(c->h_ctr->fp_sum);
+      R->fp_xor.push_back(c->h_ctr->fp_xor);
+    }
+  }
+  return TW_OK;
+}
+
+// Default of tw_config.graph_levels == 0.
+constexpr bool kGraphLevelsByDefault = false;
+
+bool graph_mode(const tw_ctx* c) {
+  if (c->cfg.time_kernels || c->cfg.graph_levels < 0) return false;
+  return c->cfg.graph_levels > 0 || kGraphLevelsByDefault;
+}
+
+// decide(k): the graph-driven loop when enabled, else (or when it gives up)
+// the host loop.
+int run_decide_any(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
+  if (graph_mode(c)) {
+    bool bailed = true;
+    int rc = run_decide_graph(c, kc, n, k, R, &bailed);
+    if (rc) return rc;
+    if (!bailed) return TW_OK;
+  }
+  return run_decide(c, kc, n, k, keep_levels, R);
+}
+
 // Backward walk through the kept levels into the device order buffer.
 int reconstruct(tw_ctx* c, KeyClass kc, int n, const DecideResult& R) {
   SmallLayout L;
@@ -435,7 +574,7 @@ int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order,
   int rc = upload_graph(c, g, kc);
   if (rc) return rc;
   DecideResult R;
-  rc = run_decide(c, kc, g.n, k, order != nullptr, &R);
+  rc = run_decide_any(c, kc, g.n, k, order != nullptr, &R);
   if (rc) {
     // the levels completed before the failure are still reported
     fill_stats(R, k, st, true);
@@ -503,7 +642,7 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
     tw = ub;
   } else {
     for (int k = k0; k < g.n; ++k) {
-      rc = run_decide(c, kc, g.n, k, want_walk, &R);
+      rc = run_decide_any(c, kc, g.n, k, want_walk, &R);
       if (rc) return rc;
       fill_stats(R, k, st, false);
       if (R.yes) {
@@ -601,7 +740,7 @@ int solve_hinted(tw_ctx* c, const HostGraph& g, float hint, int* tw_out, std::ve
   DecideResult R;
   SmallLayout L;
   auto run = [&](int k, int* yes) -> int {
-    int r = run_decide(c, kc, g.n, k, order_host != nullptr, &R);
+    int r = run_decide_any(c, kc, g.n, k, order_host != nullptr, &R);
     if (r) return r;
     fill_stats(R, k, st, false);
     *yes = R.yes;
@@ -1157,6 +1296,9 @@ int tw_create(tw_ctx** out, const tw_config* cfg) {
     return fail(TW_ERR_CUDA);
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return fail(TW_ERR_CUDA);
+  if (cudaMalloc(reinterpret_cast<void**>(&c->d_gstate), sizeof(GraphState)) != cudaSuccess ||
+      cudaHostAlloc(reinterpret_cast<void**>(&c->h_gstate), sizeof(GraphState), cudaHostAllocDefault) != cudaSuccess)
+    return fail(TW_ERR_CUDA);
   *out = c;
   return TW_OK;
 }
@@ -1169,6 +1311,9 @@ void tw_destroy(tw_ctx* c) {
     if (b->ptr) cudaFree(b->ptr);
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
+  if (c->d_gstate) cudaFree(c->d_gstate);
+  if (c->h_gstate) cudaFreeHost(c->h_gstate);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -31,70 +31,18 @@
 namespace tw {
 namespace {
 
+using core::ExpandParams;
+using core::ResidentWarps;
 using core::kFull;
-
-// Resident warps per SM the register allocation must allow: 32 for the 32-
-// and 64-bit kernels (at most 64 registers per thread, measured fastest on
-// GB300), 16 for the 128-bit kernel.
-template <class K>
-struct ResidentWarps {
-  static constexpr int value = KeyTraits<K>::kBits <= 64 ? 32 : 16;
-};
-
-template <class K>
-struct ExpandParams {
-  const K* in_keys;
-  unsigned long long n_in;
-  const K* adj;
-  int n;
-  int k;
-  K* table;
-  unsigned long long table_slots;
-  int max_probes;
-  K* out_keys;
-  uint8_t* out_pred;
-  unsigned long long out_cap;
-  LevelCounters* ctr;
-};
 
 template <class K, int kWarps>
 __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
     expand_insert_kernel(const ExpandParams<K> p) {
   constexpr int kBits = KeyTraits<K>::kBits;
   __shared__ K sAdj[kBits];
-  __shared__ K sState[kWarps][32];
-  __shared__ uint16_t sQueue[kWarps][32 * kBits];
-
-  for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
-  __syncthreads();
-
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const K valid = kfirst_n<K>(p.n);
-  unsigned long long feasible_total = 0;
-  const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
-  const unsigned long long stride = (unsigned long long)gridDim.x * kWarps;
-  core::LevelOut<K, false> out;
-  out.keys = p.out_keys;
-  out.pred = p.out_pred;
-  out.parent = nullptr;
-  out.parent_base = 0;
-  out.cap = p.out_cap;
-  out.count = &p.ctr->out_count;
-  out.overflow = &p.ctr->overflow;
-
-  for (unsigned long long chunk = (unsigned long long)blockIdx.x * kWarps + warp; chunk < n_chunks;
-       chunk += stride) {
-    const unsigned long long idx = chunk * 32ull + lane;
-    const bool active = idx < p.n_in;
-    const K S = active ? p.in_keys[idx] : valid;
-    const K feas = active ? core::feasible_extensions<K>(S, sAdj, valid, p.k) : kzero<K>();
-    const int total = core::build_queue<K>(S, feas, lane, sState[warp], sQueue[warp]);
-    feasible_total += (unsigned long long)total;
-    core::insert_queue<K, false>(sQueue[warp], sState[warp], total, lane, p.table, p.table_slots, p.max_probes, out);
-    __syncwarp();
-  }
-  if (lane == 0 && feasible_total) atomicAdd(&p.ctr->feasible, feasible_total);
+  __shared__ K sState[kWarps * 32];
+  __shared__ uint16_t sQueue[kWarps * 32 * kBits];
+  core::expand_level<K, kWarps>(p, sAdj, sState, sQueue);
 }
 
 template <class K, int kWarps>

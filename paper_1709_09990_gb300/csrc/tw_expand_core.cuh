@@ -20,6 +20,14 @@ constexpr int kMaxComps = 8;
 #define TW_INSERT_UNROLL 4  // compare-and-swaps in flight per lane
 #endif
 
+// Resident warps per SM the register allocation must allow: 32 for the 32-
+// and 64-bit kernels (at most 64 registers per thread, measured fastest on
+// GB300), 16 for the 128-bit kernel.
+template <class K>
+struct ResidentWarps {
+  static constexpr int value = KeyTraits<K>::kBits <= 64 ? 32 : 16;
+};
+
 // Home slot of a hash: the high word of hash * slots (uniform over [0, slots)
 // for any table size, so the table can be sized to the level).
 __device__ __forceinline__ unsigned long long home_slot(unsigned long long h, unsigned long long slots) {
@@ -242,6 +250,63 @@ __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, co
       }
     }
   }
+}
+
+// Parameters of one level expansion.
+template <class K>
+struct ExpandParams {
+  const K* in_keys;
+  unsigned long long n_in;
+  const K* adj;
+  int n;
+  int k;
+  K* table;
+  unsigned long long table_slots;
+  int max_probes;
+  K* out_keys;
+  uint8_t* out_pred;
+  unsigned long long out_cap;
+  LevelCounters* ctr;
+};
+
+// One level i -> i+1 by the whole block: the adjacency rows go to shared
+// memory, then each warp takes chunks of 32 consecutive states (coalesced key
+// loads), finds their feasible extensions (thread per state), queues the
+// pairs and inserts them cooperatively.  sState holds kWarps x 32 keys,
+// sQueue kWarps x 32 x kBits entries.
+template <class K, int kWarps>
+__device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, K* sState, uint16_t* sQueue) {
+  constexpr int kBits = KeyTraits<K>::kBits;
+  for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  K* sS = sState + warp * 32;
+  uint16_t* sQ = sQueue + warp * 32 * kBits;
+  const K valid = kfirst_n<K>(p.n);
+  unsigned long long feasible_total = 0;
+  const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
+  const unsigned long long stride = (unsigned long long)gridDim.x * kWarps;
+  LevelOut<K, false> out;
+  out.keys = p.out_keys;
+  out.pred = p.out_pred;
+  out.parent = nullptr;
+  out.parent_base = 0;
+  out.cap = p.out_cap;
+  out.count = &p.ctr->out_count;
+  out.overflow = &p.ctr->overflow;
+  for (unsigned long long chunk = (unsigned long long)blockIdx.x * kWarps + warp; chunk < n_chunks;
+       chunk += stride) {
+    const unsigned long long idx = chunk * 32ull + lane;
+    const bool active = idx < p.n_in;
+    const K S = active ? p.in_keys[idx] : valid;
+    const K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.k) : kzero<K>();
+    const int total = build_queue<K>(S, feas, lane, sS, sQ);
+    feasible_total += (unsigned long long)total;
+    insert_queue<K, false>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out);
+    __syncwarp();
+  }
+  if (lane == 0 && feasible_total) atomicAdd(&p.ctr->feasible, feasible_total);
 }
 
 }  // namespace core

@@ -79,6 +79,34 @@ cudaError_t launch_td(const unsigned long long* adj64, int n, int words64, const
 cudaError_t launch_bounds(const unsigned long long* adj, const int32_t* n, const int64_t* row_offset,
                           int num_graphs, int32_t* out, float* feats, cudaStream_t s);
 
+// ---- graph-driven levels (tw_graph.cu) ---------------------------------------
+// Device state of a decide run whose level loop is a captured CUDA graph: a
+// one-thread plan kernel between levels records the level just built, sizes
+// the next one and stops the run (done) or gives up (bail: the host re-runs
+// the decide with its own loop, which can grow buffers).
+struct GraphState {
+  unsigned long long level_off[130];  // arena index of level j
+  unsigned long long level_cnt[130];  // |L_j|
+  unsigned long long table_slots;     // table size of the level being built
+  unsigned long long out_off;         // arena index where it is written
+  unsigned long long out_cap;
+  unsigned long long feasible;        // feasible candidates, summed
+  unsigned long long peak_bytes;      // max kept-level + table bytes
+  int cur;                            // newest level
+  int done;
+  int bail;
+  int yes;
+};
+
+cudaError_t launch_graph_init(KeyClass kc, GraphState* st, void* keys, cudaStream_t s);
+cudaError_t launch_graph_plan(GraphState* st, LevelCounters* ctr, unsigned long long arena_cap,
+                              unsigned long long table_cap, int n, int k, int load_pct, int key_bytes, int first,
+                              cudaStream_t s);
+cudaError_t launch_graph_clear(KeyClass kc, const GraphState* st, void* table, cudaStream_t s);
+// base: in_keys/out_keys = the arena, out_pred = the predecessor arena; the
+// level fields come from st.
+cudaError_t launch_graph_expand(const GraphState* st, const ExpandLaunch& base, cudaStream_t s);
+
 // ---- batched expansion (tw_batch.cu) ---------------------------------------
 // One graph's share of a batched level step (64-bit states, n <= 64).
 struct BatchSeg {

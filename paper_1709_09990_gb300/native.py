@@ -134,7 +134,7 @@ class Context:
 
     def __init__(self, device: int = 0, fingerprints: bool = False, mem_cap_bytes: int = 0,
                  stream: int = 0, block_threads: int = 0, table_load_pct: int = 0, max_probes: int = 0,
-                 ub_shortcut: bool = False, time_kernels: bool = False):
+                 ub_shortcut: bool = False, time_kernels: bool = False, graph_levels: int = 0):
         cfg = Config()
         cfg.device = device
         cfg.fingerprints = int(fingerprints)
@@ -145,6 +145,7 @@ class Context:
         cfg.max_probes = max_probes
         cfg.ub_shortcut = int(ub_shortcut)
         cfg.time_kernels = int(time_kernels)
+        cfg.graph_levels = int(graph_levels)
         h = _vp()
         _check(lib().tw_create(ctypes.byref(h), ctypes.byref(cfg)), "tw_create")
         self._h = h

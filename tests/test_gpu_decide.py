@@ -154,3 +154,35 @@ def test_degenerate_inputs(ctx):
         ctx.decide(loop, n=9, k=3)
     with pytest.raises(native.TwError):
         ctx.decide(adj, k=-1)
+
+
+@pytest.mark.parametrize("case", ["gnp20", "u64", "u128", "rgg40_k5"])
+def test_graph_driven_levels_match_host_loop(case):
+    graphs = {"gnp20": (gg.workload_gnp20(), (6, 7, 8)), "u64": (gg.gnp(50, 0.6, 11), None),
+              "u128": (gg.gnp(80, 0.9, 120), None), "rgg40_k5": (gg.workload_rgg40(), (4, 5))}
+    adj, ks = graphs[case]
+    if ks is None:
+        lb = max(obounds.mmd(adj), obounds.mmd_plus(adj))
+        tw = oracle.solve(adj, k_start=lb, want_order=False)["tw"]
+        ks = (tw - 1, tw)
+    with context(fingerprints=True, graph_levels=-1) as host, context(fingerprints=True, graph_levels=1) as graph:
+        for k in ks:
+            a = host.decide(adj, k=k, want_order=True)
+            graph.decide(adj, k=k, want_order=True)  # first call grows the buffers
+            b = graph.decide(adj, k=k, want_order=True)
+            for key in ("level_size", "fp_sum", "fp_xor", "states_expanded", "candidates", "feasible", "levels"):
+                assert a["stats"][key] == b["stats"][key], (k, key)
+            assert a["yes"] == b["yes"]
+            if b["yes"]:
+                assert oracle.width_q(adj, b["order"].tolist()) <= k
+
+
+def test_graph_driven_solve_reuses_its_graphs():
+    adj = gg.workload_gnp20()
+    with context(graph_levels=1) as c:
+        first = c.solve(adj, want_td=True)
+        again = [c.solve(adj, want_td=True) for _ in range(3)]
+    for r in again:
+        assert r["tw"] == first["tw"] == 8
+        assert r["stats"]["states_expanded"] == first["stats"]["states_expanded"]
+        assert oracle.verify_td(adj, r["td_parent"], r["td_bags"]) == 8
