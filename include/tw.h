@@ -71,7 +71,12 @@ typedef struct {
                              forces the host loop.                               */
   int time_kernels;       /* 1 = time every expand launch with CUDA events on the
                              context's stream (fills expand_seconds)              */
-  int reserved[6];        /* must be zero                                         */
+  int autotune;           /* 1 = pick the expand block size and table load by
+                             timing the first level of >= 2^18 states once per
+                             (state width, n/8) and reuse the choice; the level
+                             is recomputed per candidate, results are unchanged.
+                             Explicit block_threads / table_load_pct win.        */
+  int reserved[5];        /* must be zero                                         */
 } tw_config;
 
 /* Per-call statistics.  Level arrays describe the last decide run. */

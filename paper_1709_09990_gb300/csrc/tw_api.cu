@@ -61,6 +61,11 @@ struct tw_ctx {
   std::vector<GraphEntry> graphs;
   GraphState* d_gstate = nullptr;
   GraphState* h_gstate = nullptr;
+  // autotuned (block threads, table load) per (key class, n / 8)
+  struct Tuned {
+    int kc, nb, block_threads, load_pct;
+  };
+  std::vector<Tuned> tuned;
 };
 
 namespace {
@@ -282,8 +287,18 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
     R->yes = 1;
     return TW_OK;
   }
-  const int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  int block_threads = c->cfg.block_threads;
   const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
+  const bool tune = c->cfg.autotune && c->cfg.table_load_pct == 0 && c->cfg.block_threads == 0;
+  bool tuned_here = false;
+  if (tune)
+    for (const auto& t : c->tuned)
+      if (t.kc == (int)kc && t.nb == n / 8) {
+        load_pct = t.load_pct;
+        block_threads = t.block_threads;
+        tuned_here = true;
+      }
   unsigned long long kept_states = 1;  // states of kept levels (keep mode)
   for (int i = 0; i <= n - k - 2; ++i) {
     const LevelRec cur = R->levels[i];
@@ -308,6 +323,61 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
         (unsigned long long)std::ceil(std::min(bound, std::max(table_est * 3.0, std::min(bound, mem_states / 4))));
     unsigned long long slots = std::max<unsigned long long>(
         64ull, (unsigned long long)std::ceil(table_est * 100.0 / load_pct));
+    // Autotune on the first large level: run it once per candidate
+    // (identical results), keep the fastest choice for this shape.
+    if (tune && !tuned_here && cur.count >= (1ull << 18)) {
+      static const int kBt[2] = {128, 256};
+      static const int kLoad[3] = {40, 50, 60};
+      float best = 1e30f;
+      int best_bt = 128, best_load = 50;
+      for (int bt : kBt)
+        for (int ld : kLoad) {
+          const unsigned long long sl =
+              std::max<unsigned long long>(64ull, (unsigned long long)std::ceil(table_est * 100.0 / ld));
+          const size_t tb = (sl * w + 15) & ~size_t(15);
+          const unsigned long long off = keep_levels ? cur.off + cur.count
+                                                     : ((out_cap <= cur.off) ? 0ull : cur.off + cur.count);
+          rc = grow(c, &c->table, tb, 0);
+          if (rc) return rc;
+          rc = grow(c, &c->keys, (size_t)(off + out_cap) * w, (size_t)(cur.off + cur.count) * w);
+          if (rc) return rc;
+          rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)(cur.off + cur.count));
+          if (rc) return rc;
+          TW_LAUNCH(c, launch_clear(c->table.ptr, tb, c->d_ctr, c->stream));
+          ExpandLaunch a;
+          a.kc = kc;
+          a.in_keys = static_cast<char*>(c->keys.ptr) + cur.off * w;
+          a.n_in = cur.count;
+          a.adj = small_at(c, L.adj);
+          a.n = n;
+          a.k = k;
+          a.table = c->table.ptr;
+          a.table_slots = sl;
+          a.max_probes = max_probes;
+          a.out_keys = static_cast<char*>(c->keys.ptr) + off * w;
+          a.out_pred = static_cast<uint8_t*>(c->pred.ptr) + off;
+          a.out_cap = out_cap;
+          a.ctr = c->d_ctr;
+          a.block_threads = bt;
+          a.grid = 0;
+          TW_CK(cudaEventRecord(c->ev0, c->stream));
+          TW_LAUNCH(c, launch_expand(a, c->stream));
+          TW_CK(cudaEventRecord(c->ev1, c->stream));
+          TW_CK(cudaStreamSynchronize(c->stream));
+          float ms = 0.f;
+          TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+          if (ms < best) {
+            best = ms;
+            best_bt = bt;
+            best_load = ld;
+          }
+        }
+      c->tuned.push_back({(int)kc, n / 8, best_bt, best_load});
+      load_pct = best_load;
+      block_threads = best_bt;
+      tuned_here = true;
+      slots = std::max<unsigned long long>(64ull, (unsigned long long)std::ceil(table_est * 100.0 / load_pct));
+    }
     LevelRec nxt;
     for (int attempt = 0;; ++attempt) {
       if (attempt > 40) return TW_ERR_CAPACITY;
@@ -340,7 +410,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       a.out_pred = static_cast<uint8_t*>(c->pred.ptr) + off;
       a.out_cap = out_cap;
       a.ctr = c->d_ctr;
-      a.block_threads = c->cfg.block_threads;
+      a.block_threads = block_threads;
       a.grid = 0;
       const bool timed = c->cfg.time_kernels != 0;
       if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
@@ -402,7 +472,10 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
   const unsigned long long arena_cap = std::min<unsigned long long>(c->keys.bytes / w, c->pred.bytes);
   const unsigned long long table_cap = c->table.bytes >= 16 ? (c->table.bytes - 16) / w : 0;
   if (arena_cap < 64 || table_cap < 64) return TW_OK;
-  const int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  if (c->cfg.autotune && c->cfg.table_load_pct == 0)
+    for (const auto& t : c->tuned)
+      if (t.kc == (int)kc && t.nb == n / 8) load_pct = t.load_pct;
   const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
   tw_ctx::GraphEntry* e = nullptr;
   for (auto& g : c->graphs)

@@ -170,3 +170,15 @@ def test_batched_path_evicts_large_levels(ctx):
     assert res["status"] == 0
     assert res["tw"].tolist() == [8, 6, 2]
     assert res["stats"]["states_expanded"] >= 79399414
+
+
+def test_autotuned_run_is_exact():
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rgg40_seed0_k6.json")))["decide"][0]
+    adj = gg.workload_rgg40()
+    with context(autotune=True, fingerprints=True) as c:
+        for _ in range(2):  # the first run tunes on its first level of >= 2^18 states
+            got = c.decide(adj, k=6)
+            assert got["stats"]["level_size"] == rec["level_size"]
+            assert [str(x) for x in got["stats"]["fp_xor"]] == rec["fp_xor"]
