@@ -53,6 +53,7 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
   int nc = 0;
   bool many = false;
   K dead = kzero<K>();
+  K bordered = kzero<K>();  // union of the kept boundaries
   K rem = S;
   while (!kempty(rem)) {
     K comp = kzero<K>();
@@ -77,6 +78,7 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
         for (int c = 0; c < kMaxComps; ++c)
           if (c == nc) comp_b[c] = bnd;
         ++nc;
+        bordered |= bnd;
       } else {
         many = true;
       }
@@ -91,11 +93,17 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
     K q = nv & ~S;
     if (kpopc(q) > k) continue;
     if (!many) {
+#ifndef TW_NO_BORDER_SKIP
+      if (ktest(bordered, v)) {
+#endif
 #pragma unroll
-      for (int c = 0; c < kMaxComps; ++c) {
-        if (c >= nc) break;
-        if (ktest(comp_b[c], v)) q |= comp_b[c];
+        for (int c = 0; c < kMaxComps; ++c) {
+          if (c >= nc) break;
+          if (ktest(comp_b[c], v)) q |= comp_b[c];
+        }
+#ifndef TW_NO_BORDER_SKIP
       }
+#endif
     } else {
       K vis = nv & S;
       K front = vis;
