@@ -574,7 +574,7 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
 }
 
 // Default of tw_config.graph_levels == 0.
-constexpr bool kGraphLevelsByDefault = false;
+constexpr bool kGraphLevelsByDefault = true;
 
 bool graph_mode(const tw_ctx* c) {
   if (c->cfg.time_kernels || c->cfg.graph_levels < 0) return false;

@@ -35,14 +35,44 @@ using core::ExpandParams;
 using core::ResidentWarps;
 using core::kFull;
 
-template <class K, int kWarps>
+template <class K, int kWarps, int U>
 __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
     expand_insert_kernel(const ExpandParams<K> p) {
   constexpr int kBits = KeyTraits<K>::kBits;
   __shared__ K sAdj[kBits];
   __shared__ K sState[kWarps * 32];
   __shared__ uint16_t sQueue[kWarps * 32 * kBits];
-  core::expand_level<K, kWarps>(p, sAdj, sState, sQueue);
+  core::expand_level<K, kWarps, U>(p, sAdj, sState, sQueue);
+}
+
+template <class K, int kWarps, int U>
+cudaError_t launch_expand_u(const ExpandParams<K>& p, unsigned long long blocks_needed, int grid, KeyClass kc,
+                            cudaStream_t s) {
+  if (grid <= 0) {
+    // resident blocks per SM x SMs, cached per (device, width, warps, U)
+    static thread_local int cached_dev = -1, cached_grid[3][3][2] = {{{0}}};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int wi = kWarps == 2 ? 0 : (kWarps == 4 ? 1 : 2);
+    const int ui = U == TW_INSERT_UNROLL ? 0 : 1;
+    if (cached_dev != dev) {
+      for (auto& a : cached_grid)
+        for (auto& r : a)
+          for (int& x : r) x = 0;
+      cached_dev = dev;
+    }
+    int& g = cached_grid[(int)kc][wi][ui];
+    if (g == 0) {
+      int sms = 0, per_sm = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_insert_kernel<K, kWarps, U>, kWarps * 32, 0);
+      g = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    grid = g;
+  }
+  if ((unsigned long long)grid > blocks_needed) grid = (int)blocks_needed;
+  expand_insert_kernel<K, kWarps, U><<<grid, kWarps * 32, 0, s>>>(p);
+  return cudaGetLastError();
 }
 
 template <class K, int kWarps>
@@ -63,29 +93,11 @@ cudaError_t launch_expand_t(const ExpandLaunch& a, cudaStream_t s) {
   if (a.n_in == 0) return cudaSuccess;
   const unsigned long long chunks = (a.n_in + 31ull) / 32ull;
   const unsigned long long blocks_needed = (chunks + kWarps - 1) / kWarps;
-  int grid = a.grid;
-  if (grid <= 0) {
-    static thread_local int cached_dev = -1, cached_grid[3][3] = {{0}};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const int kc = (int)a.kc;
-    const int wi = kWarps == 2 ? 0 : (kWarps == 4 ? 1 : 2);
-    if (cached_dev != dev) {
-      for (auto& r : cached_grid)
-        for (int& x : r) x = 0;
-      cached_dev = dev;
-    }
-    if (cached_grid[kc][wi] == 0) {
-      int sms = 0, per_sm = 0;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_insert_kernel<K, kWarps>, kWarps * 32, 0);
-      cached_grid[kc][wi] = sms * (per_sm > 0 ? per_sm : 1);
-    }
-    grid = cached_grid[kc][wi];
-  }
-  if ((unsigned long long)grid > blocks_needed) grid = (int)blocks_needed;
-  expand_insert_kernel<K, kWarps><<<grid, kWarps * 32, 0, s>>>(p);
-  return cudaGetLastError();
+  // Tables far larger than L2 miss on most probes: keep twice as many
+  // compare-and-swaps in flight per lane there.
+  if (a.table_slots * sizeof(K) > core::kDeepTableBytes)
+    return launch_expand_u<K, kWarps, 2 * TW_INSERT_UNROLL>(p, blocks_needed, a.grid, a.kc, s);
+  return launch_expand_u<K, kWarps, TW_INSERT_UNROLL>(p, blocks_needed, a.grid, a.kc, s);
 }
 
 template <class K>

@@ -17,8 +17,11 @@ namespace core {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxComps = 8;
 #ifndef TW_INSERT_UNROLL
-#define TW_INSERT_UNROLL 4  // compare-and-swaps in flight per lane
+#define TW_INSERT_UNROLL 4  // compare-and-swaps in flight per lane (L2-resident tables)
 #endif
+// Tables larger than this many bytes (about twice the L2) miss in L2 on most
+// probes; their levels run with twice as many compare-and-swaps in flight.
+constexpr unsigned long long kDeepTableBytes = 256ull << 20;
 
 // Resident warps per SM the register allocation must allow: 32 for the 32-
 // and 64-bit kernels (at most 64 registers per thread, measured fastest on
@@ -162,17 +165,16 @@ struct LevelOut {
   unsigned int* overflow;  // bit 0: output full, bit 1: probe limit
 };
 
-// Inserts the queued pairs into the table, TW_INSERT_UNROLL per lane at a
+// Inserts the queued pairs into the table, U per lane at a
 // time: the first probe of every pair is issued before any result is
 // inspected, so each lane has several compare-and-swaps in flight.  Linear
 // probing from the home slot, at most max_probes slots.  Winners append
 // (S u {v}, pred or parent) with one atomic add per round of the warp.
-template <class K, bool kParent>
+template <class K, bool kParent, int U = TW_INSERT_UNROLL>
 __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, const K* __restrict__ sS,
                                              const int total, const int lane, K* __restrict__ table,
                                              const unsigned long long slots, const int max_probes,
                                              const LevelOut<K, kParent>& out) {
-  constexpr int U = TW_INSERT_UNROLL;
   const K empty = kones<K>();
   const unsigned lanemask_lt = (1u << lane) - 1u;
   for (int base = 0; base < total; base += 32 * U) {
@@ -282,7 +284,7 @@ struct ExpandParams {
 // loads), finds their feasible extensions (thread per state), queues the
 // pairs and inserts them cooperatively.  sState holds kWarps x 32 keys,
 // sQueue kWarps x 32 x kBits entries.
-template <class K, int kWarps>
+template <class K, int kWarps, int U = TW_INSERT_UNROLL>
 __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, K* sState, uint16_t* sQueue) {
   constexpr int kBits = KeyTraits<K>::kBits;
   for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
@@ -311,7 +313,7 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
     const K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.k) : kzero<K>();
     const int total = build_queue<K>(S, feas, lane, sS, sQ);
     feasible_total += (unsigned long long)total;
-    insert_queue<K, false>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out);
+    insert_queue<K, false, U>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out);
     __syncwarp();
   }
   if (lane == 0 && feasible_total) atomicAdd(&p.ctr->feasible, feasible_total);
