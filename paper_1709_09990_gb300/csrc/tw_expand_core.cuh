@@ -57,20 +57,20 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
   bool many = false;
   K dead = kzero<K>();
   K bordered = kzero<K>();  // union of the kept boundaries
-  K rem = S;
+  K rem = S;                // vertices of S not yet in a component
   while (!kempty(rem)) {
-    K comp = kzero<K>();
-    K todo = kbit<K>(klowest(rem));
+    K todo = klsb(rem);
+    rem ^= todo;
     K bnd = kzero<K>();
     while (!kempty(todo)) {
-      const int u = klowest(todo);
-      todo = kdrop_lowest(todo);
-      comp |= kbit<K>(u);
-      const K r = sAdj[u];
+      const K b = klsb(todo);
+      todo ^= b;
+      const K r = sAdj[kindex(b)];
       bnd |= r;
-      todo |= r & rem & ~comp;
+      const K nw = r & rem;  // unvisited vertices of S next to the component
+      rem ^= nw;
+      todo |= nw;
     }
-    rem &= ~comp;
     bnd &= ~S;
     const int bs = kpopc(bnd);
     if (bs >= k + 2) {
@@ -90,38 +90,34 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
   K cand = valid & ~S & ~dead;
   K feas = kzero<K>();
   while (!kempty(cand)) {
-    const int v = klowest(cand);
-    cand = kdrop_lowest(cand);
-    const K nv = sAdj[v];
+    const K vb = klsb(cand);
+    cand ^= vb;
+    const K nv = sAdj[kindex(vb)];
     K q = nv & ~S;
     if (kpopc(q) > k) continue;
     if (!many) {
-#ifndef TW_NO_BORDER_SKIP
-      if (ktest(bordered, v)) {
-#endif
+      if (!kempty(bordered & vb)) {
 #pragma unroll
         for (int c = 0; c < kMaxComps; ++c) {
           if (c >= nc) break;
-          if (ktest(comp_b[c], v)) q |= comp_b[c];
+          if (!kempty(comp_b[c] & vb)) q |= comp_b[c];
         }
-#ifndef TW_NO_BORDER_SKIP
       }
-#endif
     } else {
       K vis = nv & S;
       K front = vis;
       while (!kempty(front)) {
-        const int u = klowest(front);
-        front = kdrop_lowest(front);
-        const K r = sAdj[u];
+        const K b = klsb(front);
+        front ^= b;
+        const K r = sAdj[kindex(b)];
         q |= r & ~S;
         const K nw = r & S & ~vis;
         vis |= nw;
         front |= nw;
       }
     }
-    q &= ~kbit<K>(v);
-    if (kpopc(q) <= k) feas |= kbit<K>(v);
+    q &= ~vb;
+    if (kpopc(q) <= k) feas |= vb;
   }
   return feas;
 }

@@ -20,6 +20,8 @@ __host__ __device__ __forceinline__ bool operator==(K128 a, K128 b) { return a.l
 __host__ __device__ __forceinline__ bool operator!=(K128 a, K128 b) { return !(a == b); }
 __host__ __device__ __forceinline__ K128& operator|=(K128& a, K128 b) { a = a | b; return a; }
 __host__ __device__ __forceinline__ K128& operator&=(K128& a, K128 b) { a = a & b; return a; }
+__host__ __device__ __forceinline__ K128 operator^(K128 a, K128 b) { return {a.lo ^ b.lo, a.hi ^ b.hi}; }
+__host__ __device__ __forceinline__ K128& operator^=(K128& a, K128 b) { a = a ^ b; return a; }
 
 template <class K> struct KeyTraits;
 template <> struct KeyTraits<uint32_t> { static constexpr int kBits = 32; static constexpr int kWords64 = 1; };
@@ -76,6 +78,18 @@ __device__ __forceinline__ unsigned long long kdrop_lowest(unsigned long long a)
 __device__ __forceinline__ K128 kdrop_lowest(K128 a) {
   return a.lo ? K128{a.lo & (a.lo - 1ull), a.hi} : K128{0ull, a.hi & (a.hi - 1ull)};
 }
+
+// Lowest set bit of a as a one-bit set (a must be non-empty for an index).
+__device__ __forceinline__ uint32_t klsb(uint32_t a) { return a & (0u - a); }
+__device__ __forceinline__ unsigned long long klsb(unsigned long long a) { return a & (0ull - a); }
+__device__ __forceinline__ K128 klsb(K128 a) {
+  return a.lo ? K128{a.lo & (0ull - a.lo), 0ull} : K128{0ull, a.hi & (0ull - a.hi)};
+}
+
+// Index of the only set bit of a one-bit set.
+__device__ __forceinline__ int kindex(uint32_t b) { return 31 - __clz(b); }
+__device__ __forceinline__ int kindex(unsigned long long b) { return 63 - __clzll(b); }
+__device__ __forceinline__ int kindex(K128 b) { return b.lo ? 63 - __clzll(b.lo) : 127 - __clzll(b.hi); }
 
 __device__ __forceinline__ bool ktest(uint32_t a, int v) { return (a >> v) & 1u; }
 __device__ __forceinline__ bool ktest(unsigned long long a, int v) { return (a >> v) & 1ull; }
