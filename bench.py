@@ -161,7 +161,8 @@ def expand_traffic():
         rec = json.load(open(os.path.join(ROOT, "profiles", "expand_insert_rgg40_traffic.json")))
     except (OSError, ValueError):
         return None
-    src = open(os.path.join(ROOT, "paper_1709_09990_gb300", "csrc", "tw_expand.cu"), "rb").read()
+    csrc = os.path.join(ROOT, "paper_1709_09990_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("tw_expand.cu", "tw_expand_core.cuh"))
     if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
     return rec.get("dram_bytes_per_launch")
@@ -251,7 +252,7 @@ def run_ours(args):
         peak = pk["hbm_gbs"] if pk else 6800.0
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                    "kernel": "expand_insert_kernel<uint64,4 warps>",
+                    "kernel": "expand_insert_kernel<uint64, 4 warps, 4 in flight>",
                     "peak_source": "measured" if pk else "fallback",
                     "bytes_per_launch": st["expand_bytes"] / max(1, st["expand_launches"]),
                     "launch_ms": 1e3 * st["expand_seconds"] / max(1, st["expand_launches"])}
