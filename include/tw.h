@@ -71,12 +71,23 @@ typedef struct {
                              forces the host loop.                               */
   int time_kernels;       /* 1 = time every expand launch with CUDA events on the
                              context's stream (fills expand_seconds)              */
+  int clique_skip;        /* 1 = Section 3.1, first optimisation: a maximum clique
+                             C (the one with the lexicographically smallest
+                             sorted vertex list) is eliminated last, so decide
+                             never adds a vertex of C and answers no at once when
+                             |C| > k+1.  Answers are unchanged, level sets shrink.
+                             tw_solve_batch ignores it.                          */
+  int disjoint_paths;     /* 1 = Section 3.1, second optimisation: decide(k) adds
+                             the edge uv for every non-adjacent pair joined by at
+                             least k+1 internally vertex-disjoint paths in G.
+                             Answers are unchanged; orderings are valid for G.
+                             tw_solve_batch ignores it.                          */
   int autotune;           /* 1 = pick the expand block size and table load by
                              timing the first level of >= 2^18 states once per
                              (state width, n/8) and reuse the choice; the level
                              is recomputed per candidate, results are unchanged.
                              Explicit block_threads / table_load_pct win.        */
-  int reserved[5];        /* must be zero                                         */
+  int reserved[3];        /* must be zero                                         */
 } tw_config;
 
 /* Per-call statistics.  Level arrays describe the last decide run. */

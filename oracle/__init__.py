@@ -64,6 +64,10 @@ def _bind(lib):
     lib.orc_subset_dp.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, _i64p, _u64p, _u64p, _intp]
     lib.orc_td_from_order.argtypes = [_u64p, ctypes.c_int, _i32p, _i32p, _u64p]
     lib.orc_verify_td.argtypes = [_u64p, ctypes.c_int, _i32p, _u64p]
+    lib.orc_max_clique.argtypes = [_u64p, ctypes.c_int, _i32p]
+    lib.orc_disjoint_paths.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.orc_decide_opts.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _u64p, _u64p, _intp,
+                                    _i64p, _i32p]
     return lib
 
 
@@ -138,6 +142,43 @@ def decide(adj: Sequence[int], k: int, want_order: bool = False) -> Dict:
             "fp_sum": fs[: lv.value].tolist(), "fp_xor": fx[: lv.value].tolist(),
             "states_expanded": int(cnt[0]), "candidates": int(cnt[1]), "feasible": int(cnt[2]),
             "order": order.tolist() if (order is not None and yes) else None}
+
+
+CLIQUE_SKIP, DISJOINT_PATHS = 1, 2
+
+
+def decide_opts(adj: Sequence[int], k: int, opts: int, want_order: bool = False) -> Dict:
+    """decide(k) with the optional reductions of Section 3.1 (opts: CLIQUE_SKIP
+    and/or DISJOINT_PATHS).  Same fields as :func:`decide`."""
+    n = len(adj)
+    r = rows(adj)
+    ls = np.zeros(n + 1, dtype=np.int64)
+    fs = np.zeros(n + 1, dtype=np.uint64)
+    fx = np.zeros(n + 1, dtype=np.uint64)
+    lv = ctypes.c_int(0)
+    cnt = np.zeros(3, dtype=np.int64)
+    order = np.full(n, -1, dtype=np.int32) if want_order else None
+    yes = _load().orc_decide_opts(_ptr(r, _u64p), n, k, opts, _ptr(ls, _i64p), _ptr(fs, _u64p), _ptr(fx, _u64p),
+                                  ctypes.byref(lv), _ptr(cnt, _i64p),
+                                  _ptr(order, _i32p) if order is not None else None)
+    if yes < 0:
+        raise ValueError("invalid graph or k")
+    return {"yes": bool(yes), "levels": lv.value, "level_size": ls[: lv.value].tolist(),
+            "fp_sum": fs[: lv.value].tolist(), "fp_xor": fx[: lv.value].tolist(),
+            "states_expanded": int(cnt[0]), "candidates": int(cnt[1]), "feasible": int(cnt[2]),
+            "order": order.tolist() if (order is not None and yes) else None}
+
+
+def max_clique(adj: Sequence[int]) -> List[int]:
+    r = rows(adj)
+    out = np.zeros(len(adj), dtype=np.int32)
+    m = _load().orc_max_clique(_ptr(r, _u64p), len(adj), _ptr(out, _i32p))
+    return out[:m].tolist()
+
+
+def disjoint_paths(adj: Sequence[int], u: int, v: int, limit: int) -> int:
+    r = rows(adj)
+    return int(_load().orc_disjoint_paths(_ptr(r, _u64p), len(adj), u, v, limit))
 
 
 def solve(adj: Sequence[int], k_start: int = 0, want_order: bool = True) -> Dict:

@@ -171,8 +171,9 @@ struct DecideOut {
   std::vector<int> order;  // filled when want_order and yes
 };
 
-// Listing 1 for one value of k, with exact sets (reading R4).
-void decide(const Graph& g, int k, bool want_order, DecideOut* out) {
+// Listing 1 for one value of k, with exact sets (reading R4).  Only vertices
+// with allowed[v] are added to sets (all of them in the plain method).
+void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::vector<char>* allowed = nullptr) {
   const int n = g.n;
   out->level_size.assign(n + 1, 0);
   out->fp_sum.assign(n + 1, 0);
@@ -195,6 +196,7 @@ void decide(const Graph& g, int k, bool want_order, DecideOut* out) {
       const Key& S = entry.first;
       for (int v = 0; v < n; ++v) {
         if (has(S, v)) continue;
+        if (allowed && !(*allowed)[v]) continue;
         ++out->candidates;
         const int degree = dfs_degree(g, S, v);
         if (degree <= k) {
@@ -551,6 +553,158 @@ int orc_verify_td(const uint64_t* adj, int n, const int32_t* parent, const uint6
     width = std::max(width, c - 1);
   }
   return width;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The first two optimisations of Section 3.1 (opt-in; they change the sets
+// explored but not the answer):
+//  * clique skip: a maximum clique C can be eliminated last, so vertices of C
+//    are never added to a set; a clique with more than k+1 vertices answers
+//    no at once.  C is the maximum clique whose sorted vertex list is
+//    lexicographically smallest.
+//  * disjoint paths: for decide(k), every non-adjacent pair u, v joined by at
+//    least k+1 internally vertex-disjoint paths in G gets the edge uv.
+namespace {
+
+// Exhaustive search over vertices in increasing order, trying "take v"
+// before "skip v"; a clique replaces the best one only when it is strictly
+// larger, so the first maximum clique found is the lexicographically smallest.
+void clique_search(const Graph& g, std::vector<int>& cur, int next, std::vector<int>& best) {
+  const int n = g.n;
+  int possible = (int)cur.size();
+  for (int v = next; v < n; ++v) {
+    bool ok = true;
+    for (int u : cur) ok = ok && g.mat[u][v];
+    if (ok) ++possible;
+  }
+  if (possible <= (int)best.size()) return;
+  if ((int)cur.size() > (int)best.size()) best = cur;
+  for (int v = next; v < n; ++v) {
+    bool ok = true;
+    for (int u : cur) ok = ok && g.mat[u][v];
+    if (!ok) continue;
+    cur.push_back(v);
+    clique_search(g, cur, v + 1, best);
+    cur.pop_back();
+  }
+}
+
+std::vector<int> first_max_clique(const Graph& g) {
+  std::vector<int> cur, best;
+  clique_search(g, cur, 0, best);
+  return best;
+}
+
+// Number of internally vertex-disjoint u-v paths, counted up to limit:
+// augmenting paths (depth-first) in the graph with every vertex other than
+// u and v split into an in- and an out-node joined by a unit arc.
+int disjoint_paths(const Graph& g, int u, int v, int limit) {
+  const int n = g.n;
+  const int N = 2 * n;  // node x_in = 2x, x_out = 2x+1
+  std::vector<std::vector<int>> cap(N, std::vector<int>(N, 0));
+  for (int x = 0; x < n; ++x) cap[2 * x][2 * x + 1] = (x == u || x == v) ? (1 << 20) : 1;
+  for (int a = 0; a < n; ++a)
+    for (int b : g.nbr[a]) cap[2 * a + 1][2 * b] = 1 << 20;
+  const int src = 2 * u + 1, dst = 2 * v;
+  int flow = 0;
+  while (flow < limit) {
+    std::vector<int> prev(N, -1);
+    std::vector<int> stack{src};
+    prev[src] = src;
+    while (!stack.empty() && prev[dst] < 0) {
+      const int x = stack.back();
+      stack.pop_back();
+      for (int y = 0; y < N; ++y)
+        if (cap[x][y] > 0 && prev[y] < 0) {
+          prev[y] = x;
+          stack.push_back(y);
+        }
+    }
+    if (prev[dst] < 0) break;
+    for (int y = dst; y != src; y = prev[y]) {
+      cap[prev[y]][y] -= 1;
+      cap[y][prev[y]] += 1;
+    }
+    ++flow;
+  }
+  return flow;
+}
+
+}  // namespace
+
+extern "C" {
+
+// The clique of the clique-skip option: writes its vertices (sorted) and
+// returns its size.
+int orc_max_clique(const uint64_t* adj, int n, int32_t* out) {
+  Graph g;
+  if (!load_graph(adj, n, &g)) return -1;
+  const std::vector<int> c = first_max_clique(g);
+  for (size_t i = 0; i < c.size(); ++i) out[i] = c[i];
+  return (int)c.size();
+}
+
+// Internally vertex-disjoint u-v paths, counted up to limit.
+int orc_disjoint_paths(const uint64_t* adj, int n, int u, int v, int limit) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || u == v || u < 0 || v < 0 || u >= n || v >= n) return -1;
+  return disjoint_paths(g, u, v, limit);
+}
+
+// orc_decide with the options of Section 3.1: bit 0 of opts = clique skip,
+// bit 1 = disjoint-path edges.  Same outputs as orc_decide; with the clique
+// skip, candidates count only vertices outside C.
+int orc_decide_opts(const uint64_t* adj, int n, int k, int opts, int64_t* level_size, uint64_t* fp_sum,
+                    uint64_t* fp_xor, int* levels, int64_t* counters, int32_t* order) {
+  Graph g0;
+  if (!load_graph(adj, n, &g0) || k < 0) return -1;
+  Graph g = g0;
+  if (opts & 2) {
+    for (int u = 0; u < n; ++u)
+      for (int v = u + 1; v < n; ++v)
+        if (!g0.mat[u][v] && disjoint_paths(g0, u, v, k + 1) >= k + 1) g.mat[u][v] = g.mat[v][u] = 1;
+    for (int u = 0; u < n; ++u) {
+      g.nbr[u].clear();
+      for (int v = 0; v < n; ++v)
+        if (g.mat[u][v]) g.nbr[u].push_back(v);
+    }
+  }
+  DecideOut out;
+  std::vector<char> allowed(n, 1);
+  const std::vector<char>* filter = nullptr;
+  bool immediate_no = false;
+  if (opts & 1) {
+    const std::vector<int> c = first_max_clique(g0);
+    for (int v : c) allowed[v] = 0;
+    filter = &allowed;
+    immediate_no = (int)c.size() > k + 1;  // tw >= |C| - 1 > k
+  }
+  if (immediate_no) {
+    out.level_size.assign(n + 1, 0);
+    out.fp_sum.assign(n + 1, 0);
+    out.fp_xor.assign(n + 1, 0);
+    out.level_size[0] = 1;
+    out.levels = 1;
+    out.yes = 0;
+  } else {
+    decide(g, k, order != nullptr, &out, filter);
+  }
+  for (int i = 0; i <= n; ++i) {
+    if (level_size) level_size[i] = out.level_size[i];
+    if (fp_sum) fp_sum[i] = out.fp_sum[i];
+    if (fp_xor) fp_xor[i] = out.fp_xor[i];
+  }
+  if (levels) *levels = out.levels;
+  if (counters) {
+    counters[0] = out.states_expanded;
+    counters[1] = out.candidates;
+    counters[2] = out.feasible;
+  }
+  if (order && out.yes)
+    for (int j = 0; j < n; ++j) order[j] = out.order[j];
+  return out.yes;
 }
 
 }  // extern "C"

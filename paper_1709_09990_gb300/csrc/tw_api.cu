@@ -53,6 +53,7 @@ struct tw_ctx {
   // graph-driven level loops, instantiated once per shape and buffer set
   struct GraphEntry {
     int kc, n, k, load, probes, bt;
+    unsigned long long allowed0, allowed1;
     void *keys, *pred, *table;
     unsigned long long arena_cap, table_cap;
     cudaGraphExec_t exec;
@@ -66,6 +67,9 @@ struct tw_ctx {
     int kc, nb, block_threads, load_pct;
   };
   std::vector<Tuned> tuned;
+  // options of Section 3.1 for the decide run being prepared
+  unsigned long long allowed[2] = {~0ull, ~0ull};
+  int skipped = 0;  // vertices excluded from the sets (|C| with the clique skip)
 };
 
 namespace {
@@ -360,6 +364,8 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
           a.ctr = c->d_ctr;
           a.block_threads = bt;
           a.grid = 0;
+          a.allowed[0] = c->allowed[0];
+          a.allowed[1] = c->allowed[1];
           TW_CK(cudaEventRecord(c->ev0, c->stream));
           TW_LAUNCH(c, launch_expand(a, c->stream));
           TW_CK(cudaEventRecord(c->ev1, c->stream));
@@ -412,6 +418,8 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       a.ctr = c->d_ctr;
       a.block_threads = block_threads;
       a.grid = 0;
+      a.allowed[0] = c->allowed[0];
+      a.allowed[1] = c->allowed[1];
       const bool timed = c->cfg.time_kernels != 0;
       if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
       TW_LAUNCH(c, launch_expand(a, c->stream));
@@ -445,7 +453,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       break;
     }
     R->states_expanded += cur.count;
-    R->candidates += cur.count * (unsigned long long)(n - i);
+    R->candidates += cur.count * (unsigned long long)(n - c->skipped - i);
     if (keep_levels) kept_states += nxt.count;
     R->levels.push_back(nxt);
     if (c->cfg.fingerprints) {
@@ -480,8 +488,9 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
   tw_ctx::GraphEntry* e = nullptr;
   for (auto& g : c->graphs)
     if (g.kc == (int)kc && g.n == n && g.k == k && g.load == load_pct && g.probes == max_probes &&
-        g.bt == c->cfg.block_threads && g.keys == c->keys.ptr && g.pred == c->pred.ptr && g.table == c->table.ptr &&
-        g.arena_cap == arena_cap && g.table_cap == table_cap)
+        g.bt == c->cfg.block_threads && g.allowed0 == c->allowed[0] && g.allowed1 == c->allowed[1] &&
+        g.keys == c->keys.ptr && g.pred == c->pred.ptr && g.table == c->table.ptr && g.arena_cap == arena_cap &&
+        g.table_cap == table_cap)
       e = &g;
   if (e == nullptr) {
     if (c->graphs.size() >= 32) {
@@ -506,6 +515,8 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
     a.ctr = c->d_ctr;
     a.block_threads = 128;
     a.grid = 0;
+    a.allowed[0] = c->allowed[0];
+    a.allowed[1] = c->allowed[1];
     cudaGraph_t graph = nullptr;
     TW_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
     int nodes = 0;
@@ -531,8 +542,8 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
     const cudaError_t inst = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     TW_CK(inst);
-    c->graphs.push_back({(int)kc, n, k, load_pct, max_probes, c->cfg.block_threads, c->keys.ptr, c->pred.ptr,
-                         c->table.ptr, arena_cap, table_cap, exec, nodes});
+    c->graphs.push_back({(int)kc, n, k, load_pct, max_probes, c->cfg.block_threads, c->allowed[0], c->allowed[1],
+                         c->keys.ptr, c->pred.ptr, c->table.ptr, arena_cap, table_cap, exec, nodes});
     e = &c->graphs.back();
   }
   TW_CK(cudaGraphLaunch(e->exec, c->stream));
@@ -551,7 +562,7 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
   for (int j = 0; j <= h.cur; ++j) R->levels.push_back({h.level_off[j], h.level_cnt[j]});
   for (int j = 0; j < h.cur; ++j) {
     R->states_expanded += h.level_cnt[j];
-    R->candidates += h.level_cnt[j] * (unsigned long long)(n - j);
+    R->candidates += h.level_cnt[j] * (unsigned long long)(n - c->skipped - j);
     R->expand_bytes += (double)(h.level_cnt[j] + 2ull * h.level_cnt[j + 1]) * (double)w + (double)h.level_cnt[j + 1];
   }
   R->feasible = h.feasible;
@@ -581,6 +592,154 @@ bool graph_mode(const tw_ctx* c) {
   return c->cfg.graph_levels > 0 || kGraphLevelsByDefault;
 }
 
+// ---- options of Section 3.1 ------------------------------------------------
+using Set128 = unsigned __int128;
+
+Set128 row_set(const HostGraph& g, int v) {
+  Set128 r = g.rows[(size_t)v * g.words];
+  if (g.words > 1) r |= (Set128)g.rows[(size_t)v * g.words + 1] << 64;
+  return r;
+}
+int popc128(Set128 a) { return __builtin_popcountll((uint64_t)a) + __builtin_popcountll((uint64_t)(a >> 64)); }
+int lowest128(Set128 a) {
+  const uint64_t lo = (uint64_t)a;
+  return lo ? __builtin_ctzll(lo) : 64 + __builtin_ctzll((uint64_t)(a >> 64));
+}
+// Sorted vertex lists compare as: A < B iff the smallest vertex in exactly
+// one of them belongs to A.
+bool lex_less(Set128 a, Set128 b) {
+  const Set128 d = a ^ b;
+  return d != 0 && ((a >> lowest128(d)) & 1);
+}
+
+// Bron-Kerbosch with pivoting over bitsets: every maximal clique is visited,
+// so every maximum one is; the lexicographically smallest maximum is kept.
+void bron_kerbosch(const std::vector<Set128>& nb, Set128 r, Set128 p, Set128 x, int* best_size, Set128* best) {
+  if (p == 0 && x == 0) {
+    const int sz = popc128(r);
+    if (sz > *best_size || (sz == *best_size && lex_less(r, *best))) {
+      *best_size = sz;
+      *best = r;
+    }
+    return;
+  }
+  if (popc128(r) + popc128(p) < *best_size) return;
+  Set128 px = p | x;
+  int pivot = lowest128(px), most = -1;
+  for (Set128 t = px; t; t &= t - 1) {
+    const int u = lowest128(t);
+    const int c = popc128(p & nb[u]);
+    if (c > most) {
+      most = c;
+      pivot = u;
+    }
+  }
+  for (Set128 t = p & ~nb[pivot]; t; t &= t - 1) {
+    const int v = lowest128(t);
+    const Set128 bv = (Set128)1 << v;
+    bron_kerbosch(nb, r | bv, p & nb[v], x & nb[v], best_size, best);
+    p &= ~bv;
+    x |= bv;
+  }
+}
+
+Set128 max_clique(const HostGraph& g) {
+  std::vector<Set128> nb(g.n);
+  for (int v = 0; v < g.n; ++v) nb[v] = row_set(g, v);
+  const Set128 all = g.n == 128 ? ~(Set128)0 : (((Set128)1 << g.n) - 1);
+  int best_size = 0;
+  Set128 best = 0;
+  bron_kerbosch(nb, 0, all, 0, &best_size, &best);
+  return best;
+}
+
+// At least t internally vertex-disjoint u-v paths (u, v not adjacent)?
+// Unit vertex capacities by splitting x into x_in -> x_out; breadth-first
+// augmenting paths in the residual network.
+bool connected_at_least(const HostGraph& g, int u, int v, int t) {
+  const int n = g.n, N = 2 * n;
+  struct Arc {
+    int to, cap, rev;
+  };
+  std::vector<std::vector<Arc>> adj(N);
+  auto add = [&](int a, int b, int cap) {
+    adj[a].push_back({b, cap, (int)adj[b].size()});
+    adj[b].push_back({a, 0, (int)adj[a].size() - 1});
+  };
+  for (int x = 0; x < n; ++x) add(2 * x, 2 * x + 1, (x == u || x == v) ? n : 1);
+  for (int a = 0; a < n; ++a)
+    for (Set128 r = row_set(g, a); r; r &= r - 1) add(2 * a + 1, 2 * lowest128(r), n);
+  const int src = 2 * u + 1, dst = 2 * v;
+  int flow = 0;
+  std::vector<int> pn(N), pa(N);
+  while (flow < t) {
+    std::fill(pn.begin(), pn.end(), -1);
+    std::vector<int> queue{src};
+    pn[src] = src;
+    for (size_t h = 0; h < queue.size() && pn[dst] < 0; ++h) {
+      const int a = queue[h];
+      for (int e = 0; e < (int)adj[a].size(); ++e) {
+        const Arc& arc = adj[a][e];
+        if (arc.cap > 0 && pn[arc.to] < 0) {
+          pn[arc.to] = a;
+          pa[arc.to] = e;
+          queue.push_back(arc.to);
+        }
+      }
+    }
+    if (pn[dst] < 0) break;
+    for (int y = dst; y != src; y = pn[y]) {
+      Arc& arc = adj[pn[y]][pa[y]];
+      arc.cap -= 1;
+      adj[y][arc.rev].cap += 1;
+    }
+    ++flow;
+  }
+  return flow >= t;
+}
+
+// Prepares decide(k) under the context's options: uploads the graph (with
+// the disjoint-path edges for this k) and sets the allowed-vertex mask.
+// *immediate_no is set when the skipped clique alone exceeds k+1 vertices.
+int prepare_options(tw_ctx* c, const HostGraph& g, int k, KeyClass kc, bool* immediate_no) {
+  *immediate_no = false;
+  c->allowed[0] = c->allowed[1] = ~0ull;
+  c->skipped = 0;
+  if (!c->cfg.clique_skip && !c->cfg.disjoint_paths) return TW_OK;
+  HostGraph gk = g;
+  if (c->cfg.disjoint_paths) {
+    for (int u = 0; u < g.n; ++u)
+      for (int v = u + 1; v < g.n; ++v) {
+        if ((row_set(g, u) >> v) & 1) continue;
+        if (!connected_at_least(g, u, v, k + 1)) continue;
+        gk.rows[(size_t)u * g.words + (v >> 6)] |= 1ull << (v & 63);
+        gk.rows[(size_t)v * g.words + (u >> 6)] |= 1ull << (u & 63);
+      }
+  }
+  int rc = upload_graph(c, gk, kc);
+  if (rc) return rc;
+  if (c->cfg.clique_skip) {
+    const Set128 cl = max_clique(g);
+    c->allowed[0] = ~(uint64_t)cl;
+    c->allowed[1] = ~(uint64_t)(cl >> 64);
+    c->skipped = popc128(cl);
+    *immediate_no = c->skipped > k + 1;
+  }
+  return TW_OK;
+}
+
+// The run of a decide answered by the clique bound alone: only L_0.
+void immediate_no_result(DecideResult* R) {
+  R->levels.assign(1, LevelRec{0, 1});
+  R->yes = 0;
+  R->states_expanded = R->candidates = R->feasible = R->retries = 0;
+  R->expand_launches = 0;
+  R->expand_seconds = R->expand_bytes = 0.0;
+  R->peak_bytes = 0;
+  R->fp_sum.assign(1, 0ull);
+  R->fp_xor.assign(1, 0ull);
+}
+
 // decide(k): the graph-driven loop when enabled, else (or when it gives up)
 // the host loop.
 int run_decide_any(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
@@ -591,6 +750,19 @@ int run_decide_any(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, Decid
     if (!bailed) return TW_OK;
   }
   return run_decide(c, kc, n, k, keep_levels, R);
+}
+
+// decide(k) under the context's options (Section 3.1's clique skip and
+// disjoint-path edges when enabled).
+int decide_with_options(tw_ctx* c, const HostGraph& g, KeyClass kc, int k, bool keep_levels, DecideResult* R) {
+  bool no = false;
+  int rc = prepare_options(c, g, k, kc, &no);
+  if (rc) return rc;
+  if (no) {
+    immediate_no_result(R);
+    return TW_OK;
+  }
+  return run_decide_any(c, kc, g.n, k, keep_levels, R);
 }
 
 // Backward walk through the kept levels into the device order buffer.
@@ -647,7 +819,7 @@ int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order,
   int rc = upload_graph(c, g, kc);
   if (rc) return rc;
   DecideResult R;
-  rc = run_decide_any(c, kc, g.n, k, order != nullptr, &R);
+  rc = decide_with_options(c, g, kc, k, order != nullptr, &R);
   if (rc) {
     // the levels completed before the failure are still reported
     fill_stats(R, k, st, true);
@@ -715,7 +887,7 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
     tw = ub;
   } else {
     for (int k = k0; k < g.n; ++k) {
-      rc = run_decide_any(c, kc, g.n, k, want_walk, &R);
+      rc = decide_with_options(c, g, kc, k, want_walk, &R);
       if (rc) return rc;
       fill_stats(R, k, st, false);
       if (R.yes) {
@@ -730,6 +902,7 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
     rc = reconstruct(c, kc, g.n, R);
     if (rc) return rc;
     int32_t* d_order = reinterpret_cast<int32_t*>(small_at(c, L.order));
+    if (c->cfg.disjoint_paths && (rc = upload_graph(c, g, kc))) return rc;  // bags of G itself
     if (td_parent || td_bags) {
       TW_LAUNCH(c, launch_td(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), g.n, g.words, d_order,
                       reinterpret_cast<int32_t*>(small_at(c, L.parent)),
@@ -813,7 +986,7 @@ int solve_hinted(tw_ctx* c, const HostGraph& g, float hint, int* tw_out, std::ve
   DecideResult R;
   SmallLayout L;
   auto run = [&](int k, int* yes) -> int {
-    int r = run_decide_any(c, kc, g.n, k, order_host != nullptr, &R);
+    int r = decide_with_options(c, g, kc, k, order_host != nullptr, &R);
     if (r) return r;
     fill_stats(R, k, st, false);
     *yes = R.yes;

@@ -90,6 +90,7 @@ cudaError_t launch_expand_t(const ExpandLaunch& a, cudaStream_t s) {
   p.out_pred = a.out_pred;
   p.out_cap = a.out_cap;
   p.ctr = a.ctr;
+  p.allowed = core::kfrom_words<K>(a.allowed[0], a.allowed[1]);
   if (a.n_in == 0) return cudaSuccess;
   const unsigned long long chunks = (a.n_in + 31ull) / 32ull;
   const unsigned long long blocks_needed = (chunks + kWarps - 1) / kWarps;

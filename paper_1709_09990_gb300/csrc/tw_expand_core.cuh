@@ -49,7 +49,7 @@ __device__ __forceinline__ unsigned long long home_slot(unsigned long long h, un
 // more falls back to a flood fill per candidate.
 template <class K>
 __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict__ sAdj, const K valid,
-                                                 const int k) {
+                                                 const K allowed, const int k) {
   K comp_b[kMaxComps];
 #pragma unroll
   for (int c = 0; c < kMaxComps; ++c) comp_b[c] = kzero<K>();
@@ -87,7 +87,7 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
       }
     }
   }
-  K cand = valid & ~S & ~dead;
+  K cand = valid & allowed & ~S & ~dead;
   K feas = kzero<K>();
   while (!kempty(cand)) {
     const K vb = klsb(cand);
@@ -258,6 +258,20 @@ __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, co
   }
 }
 
+// A key from two 64-bit words (low word first).
+template <class K> __host__ __device__ __forceinline__ K kfrom_words(unsigned long long lo, unsigned long long hi);
+template <> __host__ __device__ __forceinline__ uint32_t kfrom_words<uint32_t>(unsigned long long lo,
+                                                                                unsigned long long) {
+  return (uint32_t)lo;
+}
+template <> __host__ __device__ __forceinline__ unsigned long long kfrom_words<unsigned long long>(
+    unsigned long long lo, unsigned long long) {
+  return lo;
+}
+template <> __host__ __device__ __forceinline__ K128 kfrom_words<K128>(unsigned long long lo, unsigned long long hi) {
+  return K128{lo, hi};
+}
+
 // Parameters of one level expansion.
 template <class K>
 struct ExpandParams {
@@ -273,6 +287,7 @@ struct ExpandParams {
   uint8_t* out_pred;
   unsigned long long out_cap;
   LevelCounters* ctr;
+  K allowed;  // vertices that may be added (all by default)
 };
 
 // One level i -> i+1 by the whole block: the adjacency rows go to shared
@@ -306,7 +321,7 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;
     const K S = active ? p.in_keys[idx] : valid;
-    const K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.k) : kzero<K>();
+    const K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();
     const int total = build_queue<K>(S, feas, lane, sS, sQ);
     feasible_total += (unsigned long long)total;
     insert_queue<K, false, U>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out);

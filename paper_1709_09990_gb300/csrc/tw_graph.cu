@@ -141,6 +141,7 @@ cudaError_t expand_t(const GraphState* st, const ExpandLaunch& a, cudaStream_t s
   p.out_pred = a.out_pred;
   p.out_cap = 0;
   p.ctr = a.ctr;
+  p.allowed = core::kfrom_words<K>(a.allowed[0], a.allowed[1]);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, graph_expand_kernel<K, kWarps>, kWarps * 32, 0);
   const int grid = sm_count() * (per_sm > 0 ? per_sm : 1);

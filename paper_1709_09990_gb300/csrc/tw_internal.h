@@ -42,6 +42,7 @@ struct ExpandLaunch {
   LevelCounters* ctr;
   int block_threads;             // 64, 128 or 256
   int grid;                      // 0 = derived from the occupancy of this device
+  unsigned long long allowed[2]; // vertices that may be added (low word first)
 };
 
 cudaError_t launch_expand(const ExpandLaunch& a, cudaStream_t s);

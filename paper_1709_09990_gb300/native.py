@@ -34,7 +34,8 @@ class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("fingerprints", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t),
                 ("stream", ctypes.c_void_p), ("block_threads", ctypes.c_int), ("table_load_pct", ctypes.c_int),
                 ("max_probes", ctypes.c_int), ("ub_shortcut", ctypes.c_int), ("graph_levels", ctypes.c_int),
-                ("time_kernels", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("time_kernels", ctypes.c_int), ("clique_skip", ctypes.c_int), ("disjoint_paths", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -135,7 +136,7 @@ class Context:
     def __init__(self, device: int = 0, fingerprints: bool = False, mem_cap_bytes: int = 0,
                  stream: int = 0, block_threads: int = 0, table_load_pct: int = 0, max_probes: int = 0,
                  ub_shortcut: bool = False, time_kernels: bool = False, graph_levels: int = 0,
-                 autotune: bool = False):
+                 autotune: bool = False, clique_skip: bool = False, disjoint_paths: bool = False):
         cfg = Config()
         cfg.device = device
         cfg.fingerprints = int(fingerprints)
@@ -148,6 +149,8 @@ class Context:
         cfg.time_kernels = int(time_kernels)
         cfg.graph_levels = int(graph_levels)
         cfg.autotune = int(autotune)
+        cfg.clique_skip = int(clique_skip)
+        cfg.disjoint_paths = int(disjoint_paths)
         h = _vp()
         _check(lib().tw_create(ctypes.byref(h), ctypes.byref(cfg)), "tw_create")
         self._h = h
