@@ -45,6 +45,7 @@ struct tw_ctx {
   tw_config cfg{};
   DevBuf keys, pred, table, small;  // small: adjacency, walk, order, td scratch
   DevBuf scratch;                    // staged batch inputs/outputs and network data
+  DevBuf cand_key, cand_v, part_meta;  // regions of the partitioned insert
   LevelCounters* d_ctr = nullptr;
   LevelCounters* h_ctr = nullptr;
   int sms = 0;
@@ -140,7 +141,9 @@ int put_from_device(tw_ctx* c, void* dst, const void* src_dev, size_t bytes) {
   return TW_OK;
 }
 
-size_t total_bytes(const tw_ctx* c) { return c->keys.bytes + c->pred.bytes + c->table.bytes; }
+size_t total_bytes(const tw_ctx* c) {
+  return c->keys.bytes + c->pred.bytes + c->table.bytes + c->cand_key.bytes + c->cand_v.bytes;
+}
 
 // Grows b to at least need bytes, keeping its first keep bytes.  Growth is
 // geometric while the cap allows it.
@@ -268,6 +271,71 @@ struct DecideResult {
   double expand_seconds = 0.0, expand_bytes = 0.0;
   std::vector<unsigned long long> fp_sum, fp_xor;
 };
+
+unsigned long long partition_threshold_bytes(const tw_ctx* c) {
+  if (c->cfg.partition_table_mb == -2) return 0ull;
+  if (c->cfg.partition_table_mb < 0) return ~0ull;
+  if (c->cfg.partition_table_mb == 0) return 256ull << 20;
+  return (unsigned long long)c->cfg.partition_table_mb << 20;
+}
+
+// One level through the partitioned insert (emit, then insert range by
+// range), on a cleared table.  *fallback is set when a region overflowed
+// (the caller then runs the direct kernel on a freshly cleared table).
+int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, bool* fallback) {
+  *fallback = false;
+  const size_t w = key_bytes(a.kc);
+  const unsigned long long table_bytes = a.table_slots * w;
+  const int P = (int)std::min<unsigned long long>(kMaxRanges, std::max<unsigned long long>(2, table_bytes / (48ull << 20) + 1));
+  // input chunks whose candidate regions fit a budget of a quarter of the cap
+  const double budget = std::min<double>(16e9, (double)c->mem_cap / 4.0);
+  const double per_state = (double)std::max(1, cand_per_state) * (double)(w + 1);
+  unsigned long long chunk = (unsigned long long)std::max(1024.0, budget / (per_state * 1.2));
+  chunk = std::min<unsigned long long>(chunk, a.n_in);
+  const unsigned long long region_cap =
+      (unsigned long long)std::ceil((double)chunk * std::max(1, cand_per_state) / P * 1.15) + 4096ull;
+  int rc = grow(c, &c->cand_key, (size_t)P * region_cap * w, 0);
+  if (rc == TW_OK) rc = grow(c, &c->cand_v, (size_t)P * region_cap, 0);
+  if (rc == TW_ERR_CAPACITY) {
+    *fallback = true;
+    return TW_OK;
+  }
+  if (rc) return rc;
+  if (!c->part_meta.ptr) {
+    TW_CK(cudaMalloc(&c->part_meta.ptr, 4096));
+    c->part_meta.bytes = 4096;
+  }
+  PartitionBufs pb;
+  pb.ranges = P;
+  pb.cand_key = c->cand_key.ptr;
+  pb.cand_v = static_cast<uint8_t*>(c->cand_v.ptr);
+  pb.region_cap = region_cap;
+  pb.region_cnt = static_cast<unsigned long long*>(c->part_meta.ptr);
+  pb.prefix = pb.region_cnt + kMaxRanges;
+  pb.overflow = reinterpret_cast<unsigned int*>(pb.prefix + kMaxRanges + 1);
+  std::vector<unsigned long long> cnt(P), prefix(P + 1);
+  const size_t kw = key_bytes(a.kc);
+  for (unsigned long long lo = 0; lo < a.n_in; lo += chunk) {
+    ExpandLaunch ca = a;
+    ca.in_keys = static_cast<const char*>(a.in_keys) + lo * kw;
+    ca.n_in = std::min<unsigned long long>(chunk, a.n_in - lo);
+    TW_CK(cudaMemsetAsync(c->part_meta.ptr, 0, 4096, c->stream));
+    TW_LAUNCH(c, launch_emit(ca, pb, c->stream));
+    unsigned int ovf = 0;
+    TW_CK(cudaMemcpyAsync(cnt.data(), pb.region_cnt, P * 8, cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaMemcpyAsync(&ovf, pb.overflow, 4, cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaStreamSynchronize(c->stream));
+    if (ovf) {
+      *fallback = true;
+      return TW_OK;
+    }
+    prefix[0] = 0;
+    for (int r = 0; r < P; ++r) prefix[r + 1] = prefix[r] + std::min(cnt[r], region_cap);
+    TW_CK(cudaMemcpyAsync(pb.prefix, prefix.data(), (P + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    TW_LAUNCH(c, launch_insert_ranges(ca, pb, prefix[P], c->stream));
+  }
+  return TW_OK;
+}
 
 // One run of Listing 1 at bound k on the graph already uploaded.
 int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
@@ -422,7 +490,15 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       a.allowed[1] = c->allowed[1];
       const bool timed = c->cfg.time_kernels != 0;
       if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
-      TW_LAUNCH(c, launch_expand(a, c->stream));
+      bool direct = true;
+      if ((unsigned long long)table_bytes > partition_threshold_bytes(c)) {
+        bool fallback = false;
+        rc = run_level_partitioned(c, a, n - c->skipped - i, &fallback);
+        if (rc) return rc;
+        direct = fallback;
+        if (fallback) TW_LAUNCH(c, launch_clear(c->table.ptr, table_bytes, c->d_ctr, c->stream));
+      }
+      if (direct) TW_LAUNCH(c, launch_expand(a, c->stream));
       if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
       TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
       TW_CK(cudaStreamSynchronize(c->stream));
@@ -523,13 +599,15 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
     cudaError_t err = launch_graph_init(kc, c->d_gstate, c->keys.ptr, c->stream);
     ++nodes;
     if (err == cudaSuccess)
-      err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, n, k, load_pct, w, 1, c->stream);
+      err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, partition_threshold_bytes(c), n, k,
+                              load_pct, w, 1, c->stream);
     ++nodes;
     for (int i = 0; i <= n - k - 2 && err == cudaSuccess; ++i) {
       err = launch_graph_clear(kc, c->d_gstate, c->table.ptr, c->stream);
       if (err == cudaSuccess) err = launch_graph_expand(c->d_gstate, a, c->stream);
       if (err == cudaSuccess)
-        err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, n, k, load_pct, w, 0, c->stream);
+        err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, partition_threshold_bytes(c), n, k,
+                                load_pct, w, 0, c->stream);
       nodes += 3;
     }
     const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
@@ -1553,7 +1631,7 @@ void tw_destroy(tw_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (DevBuf* b : {&c->keys, &c->pred, &c->table, &c->small, &c->scratch})
+  for (DevBuf* b : {&c->keys, &c->pred, &c->table, &c->small, &c->scratch, &c->cand_key, &c->cand_v, &c->part_meta})
     if (b->ptr) cudaFree(b->ptr);
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);

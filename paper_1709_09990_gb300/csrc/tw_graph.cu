@@ -39,7 +39,8 @@ __global__ void graph_init_kernel(GraphState* st, K* keys) {
 // the next level: the same growth estimate and 25% table slack as the host
 // loop; the output may use the rest of the arena.
 __global__ void graph_plan_kernel(GraphState* st, LevelCounters* ctr, unsigned long long arena_cap,
-                                  unsigned long long table_cap, int n, int k, int load_pct, int w, int first) {
+                                  unsigned long long table_cap, unsigned long long direct_table_bytes, int n, int k,
+                                  int load_pct, int w, int first) {
   if (st->done || st->bail) return;
   if (!first) {
     const unsigned long long cnt = ctr->out_count;
@@ -80,7 +81,10 @@ __global__ void graph_plan_kernel(GraphState* st, LevelCounters* ctr, unsigned l
   unsigned long long slots = (unsigned long long)ceil(table_est * 100.0 / (double)load_pct);
   if (slots < 64ull) slots = 64ull;
   const unsigned long long out_off = st->level_off[i] + st->level_cnt[i];
-  if (slots > table_cap || out_off >= arena_cap || (double)(arena_cap - out_off) < table_est) {
+  // levels for the partitioned insert, and levels that do not fit, go back
+  // to the host loop
+  if (slots > table_cap || slots * (unsigned long long)w > direct_table_bytes || out_off >= arena_cap ||
+      (double)(arena_cap - out_off) < table_est) {
     st->bail = 1;
     return;
   }
@@ -161,9 +165,10 @@ cudaError_t launch_graph_init(KeyClass kc, GraphState* st, void* keys, cudaStrea
 }
 
 cudaError_t launch_graph_plan(GraphState* st, LevelCounters* ctr, unsigned long long arena_cap,
-                              unsigned long long table_cap, int n, int k, int load_pct, int key_bytes, int first,
-                              cudaStream_t s) {
-  graph_plan_kernel<<<1, 1, 0, s>>>(st, ctr, arena_cap, table_cap, n, k, load_pct, key_bytes, first);
+                              unsigned long long table_cap, unsigned long long direct_table_bytes, int n, int k,
+                              int load_pct, int key_bytes, int first, cudaStream_t s) {
+  graph_plan_kernel<<<1, 1, 0, s>>>(st, ctr, arena_cap, table_cap, direct_table_bytes, n, k, load_pct, key_bytes,
+                                    first);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,29 @@ cudaError_t launch_td(const unsigned long long* adj64, int n, int words64, const
 cudaError_t launch_bounds(const unsigned long long* adj, const int32_t* n, const int64_t* row_offset,
                           int num_graphs, int32_t* out, float* feats, cudaStream_t s);
 
+// ---- partitioned insert (tw_partition.cu) ----------------------------------
+constexpr int kMaxRanges = 64;
+
+// Candidate regions of a partitioned level: range r owns entries
+// [r * region_cap, (r + 1) * region_cap) of cand_key / cand_v.
+struct PartitionBufs {
+  int ranges;                         // P <= kMaxRanges
+  void* cand_key;                     // P * region_cap keys
+  uint8_t* cand_v;                    // P * region_cap added vertices
+  unsigned long long region_cap;
+  unsigned long long* region_cnt;     // P counters (zeroed before emit)
+  unsigned long long* prefix;         // P + 1 prefix sums of the clamped counts (for insert)
+  unsigned int* overflow;             // set when a region overflows
+};
+
+// Launch A: search + per-block counting sort of the pairs into the regions
+// (adds the feasible count to a.ctr).
+cudaError_t launch_emit(const ExpandLaunch& a, const PartitionBufs& pb, cudaStream_t s);
+// Launch B: insert the total region entries range after range into a.table,
+// appending winners to a.out_keys / a.out_pred.
+cudaError_t launch_insert_ranges(const ExpandLaunch& a, const PartitionBufs& pb, unsigned long long total,
+                                 cudaStream_t s);
+
 // ---- graph-driven levels (tw_graph.cu) ---------------------------------------
 // Device state of a decide run whose level loop is a captured CUDA graph: a
 // one-thread plan kernel between levels records the level just built, sizes
@@ -101,8 +124,8 @@ struct GraphState {
 
 cudaError_t launch_graph_init(KeyClass kc, GraphState* st, void* keys, cudaStream_t s);
 cudaError_t launch_graph_plan(GraphState* st, LevelCounters* ctr, unsigned long long arena_cap,
-                              unsigned long long table_cap, int n, int k, int load_pct, int key_bytes, int first,
-                              cudaStream_t s);
+                              unsigned long long table_cap, unsigned long long direct_table_bytes, int n, int k,
+                              int load_pct, int key_bytes, int first, cudaStream_t s);
 cudaError_t launch_graph_clear(KeyClass kc, const GraphState* st, void* table, cudaStream_t s);
 // base: in_keys/out_keys = the arena, out_pred = the predecessor arena; the
 // level fields come from st.

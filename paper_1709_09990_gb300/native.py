@@ -35,7 +35,7 @@ class Config(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("block_threads", ctypes.c_int), ("table_load_pct", ctypes.c_int),
                 ("max_probes", ctypes.c_int), ("ub_shortcut", ctypes.c_int), ("graph_levels", ctypes.c_int),
                 ("time_kernels", ctypes.c_int), ("clique_skip", ctypes.c_int), ("disjoint_paths", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("autotune", ctypes.c_int), ("partition_table_mb", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class Stats(ctypes.Structure):
@@ -136,7 +136,8 @@ class Context:
     def __init__(self, device: int = 0, fingerprints: bool = False, mem_cap_bytes: int = 0,
                  stream: int = 0, block_threads: int = 0, table_load_pct: int = 0, max_probes: int = 0,
                  ub_shortcut: bool = False, time_kernels: bool = False, graph_levels: int = 0,
-                 autotune: bool = False, clique_skip: bool = False, disjoint_paths: bool = False):
+                 autotune: bool = False, clique_skip: bool = False, disjoint_paths: bool = False,
+                 partition_table_mb: int = 0):
         cfg = Config()
         cfg.device = device
         cfg.fingerprints = int(fingerprints)
@@ -151,6 +152,7 @@ class Context:
         cfg.autotune = int(autotune)
         cfg.clique_skip = int(clique_skip)
         cfg.disjoint_paths = int(disjoint_paths)
+        cfg.partition_table_mb = int(partition_table_mb)
         h = _vp()
         _check(lib().tw_create(ctypes.byref(h), ctypes.byref(cfg)), "tw_create")
         self._h = h
