@@ -87,10 +87,12 @@ typedef struct {
                              (state width, n/8) and reuse the choice; the level
                              is recomputed per candidate, results are unchanged.
                              Explicit block_threads / table_load_pct win.        */
-  int partition_table_mb; /* levels whose hash table exceeds this many MB insert
-                             in two launches, by hash range, so that the part of
-                             the table being filled stays in L2: 0 = 256 MB,
-                             -1 = never, -2 = every level.  Results unchanged.   */
+  int partition_table_mb; /* > 0: levels whose hash table exceeds this many MB
+                             insert in two launches, by hash range, so that the
+                             part of the table being filled stays in L2; -2:
+                             every level; 0 or -1: never (default: measured
+                             slower than the direct insert on GB300 for the
+                             levels tried).  Results are unchanged.             */
   int reserved[2];        /* must be zero                                         */
 } tw_config;
 

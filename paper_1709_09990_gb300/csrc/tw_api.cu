@@ -272,10 +272,12 @@ struct DecideResult {
   std::vector<unsigned long long> fp_sum, fp_xor;
 };
 
+// Table size above which a level takes the partitioned insert (opt-in: on
+// the heavy levels measured on GB300 the direct kernel, which overlaps its
+// DRAM compare-and-swaps with the search, was 30-40% faster).
 unsigned long long partition_threshold_bytes(const tw_ctx* c) {
   if (c->cfg.partition_table_mb == -2) return 0ull;
-  if (c->cfg.partition_table_mb < 0) return ~0ull;
-  if (c->cfg.partition_table_mb == 0) return 256ull << 20;
+  if (c->cfg.partition_table_mb <= 0) return ~0ull;
   return (unsigned long long)c->cfg.partition_table_mb << 20;
 }
 
@@ -286,7 +288,11 @@ int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, 
   *fallback = false;
   const size_t w = key_bytes(a.kc);
   const unsigned long long table_bytes = a.table_slots * w;
-  const int P = (int)std::min<unsigned long long>(kMaxRanges, std::max<unsigned long long>(2, table_bytes / (48ull << 20) + 1));
+#ifndef TW_PART_SLICE_MB
+#define TW_PART_SLICE_MB 48  // table bytes per hash range: well inside the 126 MB L2
+#endif
+  const int P = (int)std::min<unsigned long long>(
+      kMaxRanges, std::max<unsigned long long>(2, table_bytes / ((unsigned long long)TW_PART_SLICE_MB << 20) + 1));
   // input chunks whose candidate regions fit a budget of a quarter of the cap
   const double budget = std::min<double>(16e9, (double)c->mem_cap / 4.0);
   const double per_state = (double)std::max(1, cand_per_state) * (double)(w + 1);

@@ -27,6 +27,55 @@ using core::ExpandParams;
 using core::kFull;
 constexpr int kWarps = 4;
 constexpr int kItemsPerThread = 4;
+#ifndef TW_PART_STREAMING
+#define TW_PART_STREAMING 1  // candidate traffic marked evict-first, so the table slice keeps L2
+#endif
+
+template <class T>
+__device__ __forceinline__ void store_stream(T* p, T v) {
+#if TW_PART_STREAMING
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
+template <class T>
+__device__ __forceinline__ T load_stream(const T* p) {
+#if TW_PART_STREAMING
+  return __ldcs(p);
+#else
+  return *p;
+#endif
+}
+__device__ __forceinline__ void store_stream(K128* p, K128 v) {
+#if TW_PART_STREAMING
+  __stcs(reinterpret_cast<ulonglong2*>(p), make_ulonglong2(v.lo, v.hi));
+#else
+  *p = v;
+#endif
+}
+__device__ __forceinline__ K128 load_stream(const K128* p) {
+#if TW_PART_STREAMING
+  const ulonglong2 t = __ldcs(reinterpret_cast<const ulonglong2*>(p));
+  return K128{t.x, t.y};
+#else
+  return *p;
+#endif
+}
+__device__ __forceinline__ void store_stream(uint8_t* p, uint8_t v) {
+#if TW_PART_STREAMING
+  __stcs(reinterpret_cast<signed char*>(p), (signed char)v);
+#else
+  *p = v;
+#endif
+}
+__device__ __forceinline__ uint8_t load_stream(const uint8_t* p) {
+#if TW_PART_STREAMING
+  return (uint8_t)__ldcs(reinterpret_cast<const signed char*>(p));
+#else
+  return *p;
+#endif
+}
 
 // Range of a hash: its high word scaled to [0, P); monotone in the hash like
 // the home slot, so range p covers a contiguous slice of the table.
@@ -90,8 +139,8 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
       const int r = range_of(khash(key), P);
       const unsigned long long pos = sBase[r] + (unsigned long long)atomicAdd(&sCursor[r], 1);
       if (pos < region_cap) {
-        cand_key[(unsigned long long)r * region_cap + pos] = key;
-        cand_v[(unsigned long long)r * region_cap + pos] = (uint8_t)(q & 0xff);
+        store_stream(&cand_key[(unsigned long long)r * region_cap + pos], key);
+        store_stream(&cand_v[(unsigned long long)r * region_cap + pos], (uint8_t)(q & 0xff));
       } else {
         atomicOr(overflow, 1u);
       }
@@ -132,8 +181,8 @@ __global__ void __launch_bounds__(256)
     if (j < total) {
       while (prefix[r + 1] <= j) ++r;
       const unsigned long long at = (unsigned long long)r * region_cap + (j - prefix[r]);
-      key[u] = cand_key[at];
-      vv[u] = cand_v[at];
+      key[u] = load_stream(&cand_key[at]);
+      vv[u] = load_stream(&cand_v[at]);
       h[u] = core::home_slot(khash(key[u]), slots);
       st[u] = 1;
     }

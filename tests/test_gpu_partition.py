@@ -19,7 +19,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 def test_partitioned_levels_match_golden(graph_levels):
     rec = json.load(open(os.path.join(GOLDEN, "rgg40_seed0_k6.json")))["decide"][0]
     adj = gg.workload_rgg40()
-    with context(fingerprints=True, partition_table_mb=1, graph_levels=graph_levels) as c:
+    with context(fingerprints=True, partition_table_mb=1, graph_levels=graph_levels) as c:  # tables > 1 MB
         for _ in range(2):
             got = c.decide(adj, k=6, want_order=True)
             assert got["stats"]["level_size"] == rec["level_size"]
