@@ -93,7 +93,12 @@ typedef struct {
                              every level; 0 or -1: never (default: measured
                              slower than the direct insert on GB300 for the
                              levels tried).  Results are unchanged.             */
-  int reserved[2];        /* must be zero                                         */
+  int mmw_prune;          /* 1 = Section 3.3: a state whose remaining graph has a
+                             minor-min-width bound (second-smallest degree of each
+                             contraction step) above k is not extended.  Answers
+                             are unchanged, level sets shrink.  Ignored by
+                             tw_solve_batch's batched kernel.                     */
+  int reserved[1];        /* must be zero                                         */
 } tw_config;
 
 /* Per-call statistics.  Level arrays describe the last decide run. */

@@ -65,6 +65,7 @@ def _bind(lib):
     lib.orc_td_from_order.argtypes = [_u64p, ctypes.c_int, _i32p, _i32p, _u64p]
     lib.orc_verify_td.argtypes = [_u64p, ctypes.c_int, _i32p, _u64p]
     lib.orc_max_clique.argtypes = [_u64p, ctypes.c_int, _i32p]
+    lib.orc_mmw_bound.argtypes = [_u64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]
     lib.orc_disjoint_paths.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.orc_decide_opts.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _u64p, _u64p, _intp,
                                     _i64p, _i32p]
@@ -144,12 +145,20 @@ def decide(adj: Sequence[int], k: int, want_order: bool = False) -> Dict:
             "order": order.tolist() if (order is not None and yes) else None}
 
 
-CLIQUE_SKIP, DISJOINT_PATHS = 1, 2
+CLIQUE_SKIP, DISJOINT_PATHS, MMW_PRUNE = 1, 2, 4
+
+
+def mmw_bound(adj: Sequence[int], s: int = 0) -> int:
+    """Minor-min-width bound (second-smallest degree per step) of the graph
+    left after eliminating the set s."""
+    r = rows(adj)
+    w0, w1 = _key_words(s)
+    return int(_load().orc_mmw_bound(_ptr(r, _u64p), len(adj), w0, w1))
 
 
 def decide_opts(adj: Sequence[int], k: int, opts: int, want_order: bool = False) -> Dict:
-    """decide(k) with the optional reductions of Section 3.1 (opts: CLIQUE_SKIP
-    and/or DISJOINT_PATHS).  Same fields as :func:`decide`."""
+    """decide(k) with the optional reductions of Sections 3.1 and 3.3 (opts:
+    CLIQUE_SKIP, DISJOINT_PATHS, MMW_PRUNE).  Same fields as :func:`decide`."""
     n = len(adj)
     r = rows(adj)
     ls = np.zeros(n + 1, dtype=np.int64)

@@ -171,9 +171,14 @@ struct DecideOut {
   std::vector<int> order;  // filled when want_order and yes
 };
 
+int mmw_bound(const Graph& g, const Key& S, int stop_above);
+
 // Listing 1 for one value of k, with exact sets (reading R4).  Only vertices
-// with allowed[v] are added to sets (all of them in the plain method).
-void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::vector<char>* allowed = nullptr) {
+// with allowed[v] are added to sets (all of them in the plain method).  With
+// mmw_prune, a set whose remaining graph has a minor-min-width bound above k
+// (Section 3.3) is not extended.
+void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::vector<char>* allowed = nullptr,
+            bool mmw_prune = false) {
   const int n = g.n;
   out->level_size.assign(n + 1, 0);
   out->fp_sum.assign(n + 1, 0);
@@ -194,10 +199,14 @@ void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::v
     std::unordered_map<Key, int, KeyHash> outp;
     for (const auto& entry : inp) {
       const Key& S = entry.first;
+      int free_vertices = 0;
+      for (int v = 0; v < n; ++v)
+        if (!has(S, v) && (!allowed || (*allowed)[v])) ++free_vertices;
+      out->candidates += free_vertices;
+      if (mmw_prune && mmw_bound(g, S, k) > k) continue;
       for (int v = 0; v < n; ++v) {
         if (has(S, v)) continue;
         if (allowed && !(*allowed)[v]) continue;
-        ++out->candidates;
         const int degree = dfs_degree(g, S, v);
         if (degree <= k) {
           ++out->feasible;
@@ -591,6 +600,59 @@ void clique_search(const Graph& g, std::vector<int>& cur, int next, std::vector<
   }
 }
 
+// Minor-min-width of the graph H that remains after eliminating S
+// (Section 3.3), with the second-smallest degree as the bound of each step:
+// H has the vertices outside S and an edge uw iff w is in Q(S, u).  While H
+// has at least two vertices: take a minimum-degree vertex v (lowest index),
+// record the second-smallest degree of H, delete v if it is isolated, else
+// contract v into its minimum-degree neighbour (lowest index).  Returns the
+// largest recorded degree (callers only compare it with stop_above, so the
+// search may stop once it exceeds that).
+int mmw_bound(const Graph& g, const Key& S, int stop_above) {
+  const int n = g.n;
+  std::vector<std::vector<char>> h(n, std::vector<char>(n, 0));
+  std::vector<char> alive(n, 0);
+  for (int u = 0; u < n; ++u) {
+    if (has(S, u)) continue;
+    alive[u] = 1;
+    const Key q = q_set(g, S, u);
+    for (int w = 0; w < n; ++w)
+      if (has(q, w)) h[u][w] = 1;
+  }
+  int lb = 0;
+  for (;;) {
+    std::vector<int> deg(n, -1);
+    int count = 0;
+    for (int u = 0; u < n; ++u) {
+      if (!alive[u]) continue;
+      ++count;
+      int d = 0;
+      for (int w = 0; w < n; ++w) d += (alive[w] && h[u][w]) ? 1 : 0;
+      deg[u] = d;
+    }
+    if (count < 2) break;
+    int v = -1;
+    for (int u = 0; u < n; ++u)
+      if (alive[u] && (v < 0 || deg[u] < deg[v])) v = u;
+    int second = -1;
+    for (int u = 0; u < n; ++u)
+      if (alive[u] && u != v && (second < 0 || deg[u] < second)) second = deg[u];
+    lb = std::max(lb, second);
+    if (lb > stop_above) return lb;
+    if (deg[v] == 0) {
+      alive[v] = 0;
+      continue;
+    }
+    int into = -1;
+    for (int u = 0; u < n; ++u)
+      if (alive[u] && h[v][u] && (into < 0 || deg[u] < deg[into])) into = u;
+    for (int w = 0; w < n; ++w)
+      if (alive[w] && h[v][w] && w != into) h[into][w] = h[w][into] = 1;
+    alive[v] = 0;
+  }
+  return lb;
+}
+
 std::vector<int> first_max_clique(const Graph& g) {
   std::vector<int> cur, best;
   clique_search(g, cur, 0, best);
@@ -636,6 +698,13 @@ int disjoint_paths(const Graph& g, int u, int v, int limit) {
 
 extern "C" {
 
+// The minor-min-width bound of the graph left after eliminating S.
+int orc_mmw_bound(const uint64_t* adj, int n, uint64_t s0, uint64_t s1) {
+  Graph g;
+  if (!load_graph(adj, n, &g)) return -1;
+  return mmw_bound(g, Key{{s0, s1}}, n);
+}
+
 // The clique of the clique-skip option: writes its vertices (sorted) and
 // returns its size.
 int orc_max_clique(const uint64_t* adj, int n, int32_t* out) {
@@ -653,9 +722,10 @@ int orc_disjoint_paths(const uint64_t* adj, int n, int u, int v, int limit) {
   return disjoint_paths(g, u, v, limit);
 }
 
-// orc_decide with the options of Section 3.1: bit 0 of opts = clique skip,
-// bit 1 = disjoint-path edges.  Same outputs as orc_decide; with the clique
-// skip, candidates count only vertices outside C.
+// orc_decide with the options of Sections 3.1 and 3.3: bit 0 of opts =
+// clique skip, bit 1 = disjoint-path edges, bit 2 = minor-min-width pruning
+// (on the graph with the added edges).  Same outputs as orc_decide; with the
+// clique skip, candidates count only vertices outside C.
 int orc_decide_opts(const uint64_t* adj, int n, int k, int opts, int64_t* level_size, uint64_t* fp_sum,
                     uint64_t* fp_xor, int* levels, int64_t* counters, int32_t* order) {
   Graph g0;
@@ -689,7 +759,7 @@ int orc_decide_opts(const uint64_t* adj, int n, int k, int opts, int64_t* level_
     out.levels = 1;
     out.yes = 0;
   } else {
-    decide(g, k, order != nullptr, &out, filter);
+    decide(g, k, order != nullptr, &out, filter, (opts & 4) != 0);
   }
   for (int i = 0; i <= n; ++i) {
     if (level_size) level_size[i] = out.level_size[i];

@@ -440,6 +440,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
           a.grid = 0;
           a.allowed[0] = c->allowed[0];
           a.allowed[1] = c->allowed[1];
+          a.mmw = c->cfg.mmw_prune ? 1 : 0;
           TW_CK(cudaEventRecord(c->ev0, c->stream));
           TW_LAUNCH(c, launch_expand(a, c->stream));
           TW_CK(cudaEventRecord(c->ev1, c->stream));
@@ -494,6 +495,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       a.grid = 0;
       a.allowed[0] = c->allowed[0];
       a.allowed[1] = c->allowed[1];
+      a.mmw = c->cfg.mmw_prune ? 1 : 0;
       const bool timed = c->cfg.time_kernels != 0;
       if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
       bool direct = true;
@@ -599,6 +601,7 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
     a.grid = 0;
     a.allowed[0] = c->allowed[0];
     a.allowed[1] = c->allowed[1];
+    a.mmw = c->cfg.mmw_prune ? 1 : 0;
     cudaGraph_t graph = nullptr;
     TW_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
     int nodes = 0;

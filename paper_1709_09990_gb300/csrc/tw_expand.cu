@@ -35,14 +35,14 @@ using core::ExpandParams;
 using core::ResidentWarps;
 using core::kFull;
 
-template <class K, int kWarps, int U>
+template <class K, int kWarps, int U, bool kMMW = false>
 __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
     expand_insert_kernel(const ExpandParams<K> p) {
   constexpr int kBits = KeyTraits<K>::kBits;
   __shared__ K sAdj[kBits];
   __shared__ K sState[kWarps * 32];
   __shared__ uint16_t sQueue[kWarps * 32 * kBits];
-  core::expand_level<K, kWarps, U>(p, sAdj, sState, sQueue);
+  core::expand_level<K, kWarps, U, kMMW>(p, sAdj, sState, sQueue);
 }
 
 template <class K, int kWarps, int U>
@@ -91,9 +91,22 @@ cudaError_t launch_expand_t(const ExpandLaunch& a, cudaStream_t s) {
   p.out_cap = a.out_cap;
   p.ctr = a.ctr;
   p.allowed = core::kfrom_words<K>(a.allowed[0], a.allowed[1]);
+  p.mmw = a.mmw;
   if (a.n_in == 0) return cudaSuccess;
   const unsigned long long chunks = (a.n_in + 31ull) / 32ull;
   const unsigned long long blocks_needed = (chunks + kWarps - 1) / kWarps;
+  if (a.mmw) {
+    // minor-min-width pruning (opt-in): its own instantiation, 4 warps
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_insert_kernel<K, 4, TW_INSERT_UNROLL, true>, 128, 0);
+    unsigned long long grid = (unsigned long long)sms * (per_sm > 0 ? per_sm : 1);
+    const unsigned long long need = (chunks + 3) / 4;
+    if (grid > need) grid = need;
+    expand_insert_kernel<K, 4, TW_INSERT_UNROLL, true><<<(int)grid, 128, 0, s>>>(p);
+    return cudaGetLastError();
+  }
   // Tables far larger than L2 miss on most probes: keep twice as many
   // compare-and-swaps in flight per lane there.
   if (a.table_slots * sizeof(K) > core::kDeepTableBytes)

@@ -122,6 +122,129 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
   return feas;
 }
 
+// Warp-wide minimum of (d, v), lowest v on ties; v < 0 means none.
+__device__ __forceinline__ void warp_min_pair(int& d, int& v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const int od = __shfl_xor_sync(kFull, d, off);
+    const int ov = __shfl_xor_sync(kFull, v, off);
+    if (ov >= 0 && (v < 0 || od < d || (od == d && ov < v))) {
+      d = od;
+      v = ov;
+    }
+  }
+}
+
+// Does the minor-min-width bound of the graph H left after eliminating S
+// exceed k (Section 3.3, with the second-smallest degree of each minor as the
+// bound, which is also a treewidth lower bound)?  Warp-cooperative: every
+// lane passes the same S; lane l owns the vertices l, l+32, ... and their rows
+// of H (row of v = Q(S, v), found by a flood fill through S).  While H has
+// more than k+1 vertices: take a minimum-degree vertex v (lowest index),
+// record the second-smallest degree, delete v if isolated, else contract it
+// into its minimum-degree neighbour (lowest index).  With at most k+1
+// vertices left no degree can exceed k, so the answer is settled.
+template <class K>
+__device__ __forceinline__ bool mmw_exceeds(const K S, const K* __restrict__ sAdj, const int n, const int k,
+                                            const int lane) {
+  constexpr int NV = KeyTraits<K>::kBits / 32;  // vertices per lane
+  constexpr int kNone = 1 << 30;
+  K alive = kfirst_n<K>(n) & ~S;
+  K row[NV];
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const int v = lane + 32 * t;
+    row[t] = kzero<K>();
+    if (v < n && ktest(alive, v)) {
+      const K nv = sAdj[v];
+      K q = nv & ~S;
+      K vis = nv & S;
+      K front = vis;
+      while (!kempty(front)) {
+        const K b = klsb(front);
+        front ^= b;
+        const K r = sAdj[kindex(b)];
+        q |= r & ~S;
+        const K nw = r & S & ~vis;
+        vis |= nw;
+        front |= nw;
+      }
+      row[t] = q & ~kbit<K>(v);
+    }
+  }
+  int count = kpopc(alive);
+  int lb = 0;
+  while (count > k + 1) {
+    int deg[NV];
+    int dmin = kNone, vmin = -1;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int v = lane + 32 * t;
+      deg[t] = (v < n && ktest(alive, v)) ? kpopc(row[t] & alive) : kNone;
+      if (deg[t] < dmin) {
+        dmin = deg[t];
+        vmin = v;
+      }
+    }
+    warp_min_pair(dmin, vmin);
+    int d2 = kNone, v2 = -1;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int v = lane + 32 * t;
+      if (v != vmin && deg[t] < d2) {
+        d2 = deg[t];
+        v2 = v;
+      }
+    }
+    warp_min_pair(d2, v2);
+    lb = max(lb, d2);
+    if (lb > k) return true;
+    const K bv = kbit<K>(vmin);
+    alive &= ~bv;
+    --count;
+    if (dmin == 0) continue;
+    K mine = kzero<K>();
+#pragma unroll
+    for (int t = 0; t < NV; ++t)
+      if (t == (vmin >> 5)) mine = row[t];
+    const K rv = kshfl(mine, vmin & 31) & alive;
+    int du = kNone, u = -1;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int v = lane + 32 * t;
+      if (v < n && ktest(rv, v) && deg[t] < du) {
+        du = deg[t];
+        u = v;
+      }
+    }
+    warp_min_pair(du, u);
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int v = lane + 32 * t;
+      if (v == u)
+        row[t] |= rv & ~kbit<K>(u);
+      else if (v < n && ktest(rv, v))
+        row[t] |= kbit<K>(u);
+    }
+  }
+  return false;
+}
+
+// Drops the extensions of every state of the warp whose remaining graph has
+// a minor-min-width bound above k (the warp examines its states one by one).
+template <class K>
+__device__ __forceinline__ K mmw_filter(const K S, K feas, const K* __restrict__ sAdj, const int n, const int k,
+                                        const int lane) {
+  unsigned pending = __ballot_sync(kFull, !kempty(feas));
+  while (pending) {
+    const int j = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const bool prune = mmw_exceeds<K>(kshfl(S, j), sAdj, n, k, lane);
+    if (prune && lane == j) feas = kzero<K>();
+  }
+  return feas;
+}
+
 // Packs the feasible (S, v) pairs of the warp's 32 states into the warp's
 // queue (entry = lane << 8 | v) and stores each lane's S; returns the number
 // of pairs (warp uniform).
@@ -288,6 +411,7 @@ struct ExpandParams {
   unsigned long long out_cap;
   LevelCounters* ctr;
   K allowed;  // vertices that may be added (all by default)
+  int mmw;    // 1: minor-min-width pruning of the states before they are extended
 };
 
 // One level i -> i+1 by the whole block: the adjacency rows go to shared
@@ -295,7 +419,7 @@ struct ExpandParams {
 // loads), finds their feasible extensions (thread per state), queues the
 // pairs and inserts them cooperatively.  sState holds kWarps x 32 keys,
 // sQueue kWarps x 32 x kBits entries.
-template <class K, int kWarps, int U = TW_INSERT_UNROLL>
+template <class K, int kWarps, int U = TW_INSERT_UNROLL, bool kMMW = false>
 __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, K* sState, uint16_t* sQueue) {
   constexpr int kBits = KeyTraits<K>::kBits;
   for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
@@ -321,7 +445,8 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;
     const K S = active ? p.in_keys[idx] : valid;
-    const K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();
+    K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();
+    if (kMMW) feas = mmw_filter<K>(S, feas, sAdj, p.n, p.k, lane);
     const int total = build_queue<K>(S, feas, lane, sS, sQ);
     feasible_total += (unsigned long long)total;
     insert_queue<K, false, U>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out);

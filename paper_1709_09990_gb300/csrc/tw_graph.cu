@@ -104,7 +104,7 @@ __global__ void graph_clear_kernel(const GraphState* __restrict__ st, uint4* __r
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) t[i] = ones;
 }
 
-template <class K, int kWarps>
+template <class K, int kWarps, bool kMMW>
 __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
     graph_expand_kernel(const GraphState* __restrict__ st, const ExpandParams<K> base) {
   constexpr int kBits = KeyTraits<K>::kBits;
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
   p.out_pred = base.out_pred + st->out_off;
   p.out_cap = st->out_cap;
   p.table_slots = st->table_slots;
-  core::expand_level<K, kWarps>(p, sAdj, sState, sQueue);
+  core::expand_level<K, kWarps, TW_INSERT_UNROLL, kMMW>(p, sAdj, sState, sQueue);
 }
 
 int sm_count() {
@@ -146,10 +146,15 @@ cudaError_t expand_t(const GraphState* st, const ExpandLaunch& a, cudaStream_t s
   p.out_cap = 0;
   p.ctr = a.ctr;
   p.allowed = core::kfrom_words<K>(a.allowed[0], a.allowed[1]);
+  p.mmw = a.mmw;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, graph_expand_kernel<K, kWarps>, kWarps * 32, 0);
-  const int grid = sm_count() * (per_sm > 0 ? per_sm : 1);
-  graph_expand_kernel<K, kWarps><<<grid, kWarps * 32, 0, s>>>(st, p);
+  if (a.mmw) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, graph_expand_kernel<K, kWarps, true>, kWarps * 32, 0);
+    graph_expand_kernel<K, kWarps, true><<<sm_count() * (per_sm > 0 ? per_sm : 1), kWarps * 32, 0, s>>>(st, p);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, graph_expand_kernel<K, kWarps, false>, kWarps * 32, 0);
+    graph_expand_kernel<K, kWarps, false><<<sm_count() * (per_sm > 0 ? per_sm : 1), kWarps * 32, 0, s>>>(st, p);
+  }
   return cudaGetLastError();
 }
 

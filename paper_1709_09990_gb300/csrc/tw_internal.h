@@ -43,6 +43,7 @@ struct ExpandLaunch {
   int block_threads;             // 64, 128 or 256
   int grid;                      // 0 = derived from the occupancy of this device
   unsigned long long allowed[2]; // vertices that may be added (low word first)
+  int mmw;                       // 1: minor-min-width pruning (Section 3.3)
 };
 
 cudaError_t launch_expand(const ExpandLaunch& a, cudaStream_t s);

@@ -95,6 +95,15 @@ __device__ __forceinline__ bool ktest(uint32_t a, int v) { return (a >> v) & 1u;
 __device__ __forceinline__ bool ktest(unsigned long long a, int v) { return (a >> v) & 1ull; }
 __device__ __forceinline__ bool ktest(K128 a, int v) { return v < 64 ? ((a.lo >> v) & 1ull) : ((a.hi >> (v - 64)) & 1ull); }
 
+// Warp shuffle of a key from lane src.
+__device__ __forceinline__ uint32_t kshfl(uint32_t a, int src) { return __shfl_sync(0xffffffffu, a, src); }
+__device__ __forceinline__ unsigned long long kshfl(unsigned long long a, int src) {
+  return __shfl_sync(0xffffffffu, a, src);
+}
+__device__ __forceinline__ K128 kshfl(K128 a, int src) {
+  return K128{__shfl_sync(0xffffffffu, a.lo, src), __shfl_sync(0xffffffffu, a.hi, src)};
+}
+
 // ---- hashing ----------------------------------------------------------------
 // 64-bit finaliser of MurmurHash3 (Appleby); the paper also hashes states with
 // Murmur3 (Section 3.2).

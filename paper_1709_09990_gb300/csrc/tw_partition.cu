@@ -105,7 +105,8 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
     const unsigned long long idx = b * (kWarps * 32) + warp * 32 + lane;
     const bool active = idx < p.n_in;
     const K S = active ? p.in_keys[idx] : valid;
-    const K feas = active ? core::feasible_extensions<K>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();
+    K feas = active ? core::feasible_extensions<K>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();
+    if (p.mmw) feas = core::mmw_filter<K>(S, feas, sAdj, p.n, p.k, lane);
     const int total = core::build_queue<K>(S, feas, lane, sState + warp * 32, sQueue + warp * 32 * kBits);
     if (lane == 0) sTotal[warp] = total;
     for (int r = threadIdx.x; r < P; r += blockDim.x) sHist[r] = 0;
@@ -268,6 +269,7 @@ cudaError_t emit_t(const ExpandLaunch& a, const PartitionBufs& pb, cudaStream_t 
   p.out_cap = a.out_cap;
   p.ctr = a.ctr;
   p.allowed = core::kfrom_words<K>(a.allowed[0], a.allowed[1]);
+  p.mmw = a.mmw;
   const unsigned long long blocks_needed = (a.n_in + kWarps * 32 - 1) / (kWarps * 32);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_kernel<K>, kWarps * 32, 0);

@@ -113,6 +113,7 @@ extern "C" int tw_expand_level_static(const uint64_t* d_in_keys, uint64_t n_in, 
   a.grid = 0;
   a.allowed[0] = ~0ull;
   a.allowed[1] = ~0ull;
+  a.mmw = 0;
   if (launch_expand(a, s) != cudaSuccess) {
     cudaGetLastError();
     return TW_ERR_CUDA;

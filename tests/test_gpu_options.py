@@ -10,8 +10,10 @@ from tests.gpu_util import context
 
 pytestmark = pytest.mark.gpu
 
-OPTS = {"clique": (True, False, oracle.CLIQUE_SKIP), "paths": (False, True, oracle.DISJOINT_PATHS),
-        "both": (True, True, oracle.CLIQUE_SKIP | oracle.DISJOINT_PATHS)}
+OPTS = {"clique": (True, False, False, oracle.CLIQUE_SKIP), "paths": (False, True, False, oracle.DISJOINT_PATHS),
+        "both": (True, True, False, oracle.CLIQUE_SKIP | oracle.DISJOINT_PATHS),
+        "mmw": (False, False, True, oracle.MMW_PRUNE),
+        "all": (True, True, True, oracle.CLIQUE_SKIP | oracle.DISJOINT_PATHS | oracle.MMW_PRUNE)}
 
 
 def _check(ctx, adj, k, o):
@@ -28,12 +30,12 @@ def _check(ctx, adj, k, o):
 @pytest.mark.parametrize("name", sorted(OPTS))
 @pytest.mark.parametrize("graph_levels", [-1, 1])
 def test_options_match_oracle(name, graph_levels):
-    cs, dp, o = OPTS[name]
+    cs, dp, mm, o = OPTS[name]
     # (dense graphs make the oracle's exhaustive clique search slow; the
     # 128-bit states are covered by a relabelled path on 70 vertices)
     graphs = [gg.workload_gnp20(), gg.gnp(44, 0.5, 4), gg.relabel(gg.path(70), 5), gg.partial_ktree(26, 5, 3)]
     graphs += [gg.gnp(14 + s, 0.35, 4000 + s) for s in range(6)]
-    with context(fingerprints=True, clique_skip=cs, disjoint_paths=dp, graph_levels=graph_levels) as ctx:
+    with context(fingerprints=True, clique_skip=cs, disjoint_paths=dp, mmw_prune=mm, graph_levels=graph_levels) as ctx:
         for adj in graphs:
             lb = max(obounds.mmd(adj), obounds.mmd_plus(adj))
             tw = oracle.solve(adj, k_start=lb, want_order=False)["tw"]
@@ -44,8 +46,8 @@ def test_options_match_oracle(name, graph_levels):
 
 @pytest.mark.parametrize("name", sorted(OPTS))
 def test_solve_with_options_is_exact(name):
-    cs, dp, _ = OPTS[name]
-    with context(clique_skip=cs, disjoint_paths=dp) as ctx:
+    cs, dp, mm, _ = OPTS[name]
+    with context(clique_skip=cs, disjoint_paths=dp, mmw_prune=mm) as ctx:
         for s in range(8):
             adj = gg.mixed_graph(6000 + s, 10, 26, s % 2 == 0)
             tw = oracle.solve(adj, want_order=False)["tw"] if len(adj) <= 18 else None

@@ -9,7 +9,8 @@ import pytest
 import oracle
 from paper_1709_09990_gb300 import graphgen as gg
 
-OPTS = (oracle.CLIQUE_SKIP, oracle.DISJOINT_PATHS, oracle.CLIQUE_SKIP | oracle.DISJOINT_PATHS)
+OPTS = (oracle.CLIQUE_SKIP, oracle.DISJOINT_PATHS, oracle.CLIQUE_SKIP | oracle.DISJOINT_PATHS, oracle.MMW_PRUNE,
+        oracle.CLIQUE_SKIP | oracle.DISJOINT_PATHS | oracle.MMW_PRUNE)
 
 
 def _graphs(count, lo, hi, seed0):
@@ -86,3 +87,46 @@ def test_closed_forms_with_clique_skip():
     # K_{a,b} with a <= b: vertices on the b side have a disjoint paths
     g = gg.complete_bipartite(3, 5)
     assert oracle.disjoint_paths(g, 3, 4, 10) == 3 and oracle.disjoint_paths(g, 0, 1, 10) == 5
+
+
+def _eliminated_graph(adj, S):
+    """The graph left after eliminating the vertices of S one by one (each
+    turns its neighbourhood into a clique), relabelled to 0..n-|S|-1."""
+    n = len(adj)
+    nb = {v: {u for u in range(n) if (adj[v] >> u) & 1} for v in range(n)}
+    for v in range(n):
+        if (S >> v) & 1:
+            for a in nb[v]:
+                nb[a].discard(v)
+                nb[a] |= nb[v] - {a}
+            del nb[v]
+    keep = sorted(nb)
+    pos = {v: i for i, v in enumerate(keep)}
+    return [sum(1 << pos[u] for u in nb[v]) for v in keep]
+
+
+def test_mmw_bound_is_a_lower_bound_of_the_remaining_graph():
+    from oracle import bounds
+    for adj in _graphs(60, 2, 10, 9500):
+        n = len(adj)
+        tw = oracle.brute_force_tw(adj)
+        assert bounds.mmd_plus(adj) <= oracle.mmw_bound(adj, 0) <= tw
+        rng = gg.Rng(n * 31 + 7)
+        for _ in range(3):
+            S = sum(1 << v for v in range(n) if rng.uniform() < 0.4)
+            if bin(S).count("1") == n:
+                continue
+            H = _eliminated_graph(adj, S)
+            assert oracle.mmw_bound(adj, S) <= oracle.brute_force_tw(H)
+
+
+def test_mmw_bound_closed_forms():
+    for n in range(2, 9):
+        assert oracle.mmw_bound(gg.complete(n)) == n - 1
+    for n in range(3, 10):
+        assert oracle.mmw_bound(gg.cycle(n)) == 2
+        assert oracle.mmw_bound(gg.path(n)) == 1
+    # the second-smallest degree can exceed the smallest: a triangle with a
+    # pendant vertex has degrees 1, 2, 2, 3 and tw 2
+    g = [0b0110, 0b1101, 0b0011, 0b0010]
+    assert oracle.mmw_bound(g) == 2
