@@ -1,0 +1,477 @@
+// Host driver of tw_solve_batch (see the section comment below and
+// tw_batch.cu for the kernels).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tw_host.h"
+
+namespace tw {
+namespace host {
+
+// ---------------------------------------------------------------- batches
+//
+// Level-synchronous batched solve for graphs with n <= 64.  Every graph runs
+// its own k sweep (Section 3.1) as a small state machine on the host; each
+// step expands the current level of every running graph in one launch of
+// expand_batch_kernel.  A graph whose level would exceed kEvictStates leaves
+// the batch and is solved afterwards by the single-graph path, which sizes
+// its buffers for large levels.
+constexpr double kEvictStates = double(1 << 21);
+constexpr unsigned long long kStepSlots = 1ull << 27;   // table slots per step
+constexpr unsigned long long kStepOut = 1ull << 26;     // output states per step
+constexpr int kBatchProbes = 256;
+
+struct BGraph {
+  int in_idx = 0;
+  int n = 0;
+  int lb = 0;
+  int k0 = 0;
+  int k = -1;
+  int yes_min = 1 << 30;
+  int no_max = -1;
+  int state = 0;  // 0 running, 1 done, 2 evicted
+  std::vector<LevelRec> levels;
+  double table_mult = 1.0;
+  unsigned long long ocap_retry = 0;
+  int tw = -1;
+  int64_t order_off = 0;
+};
+
+template <class T>
+int dev_alloc(T** p, size_t count) {
+  void* v = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&v, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return TW_ERR_CAPACITY;
+  }
+  *p = static_cast<T*>(v);
+  return TW_OK;
+}
+
+struct BatchRun {
+  tw_ctx* c;
+  std::vector<BGraph> g;
+  unsigned long long* adj = nullptr;
+  unsigned long long* akeys = nullptr;
+  uint32_t* apar = nullptr;
+  unsigned long long acap = 0, atop = 0;
+  unsigned long long* table = nullptr;
+  unsigned long long tcap = 0;
+  unsigned long long* okeys = nullptr;
+  uint32_t* opar = nullptr;
+  unsigned long long ocap = 0;
+  BatchSeg* segs = nullptr;
+  unsigned long long* cbeg = nullptr;
+  BatchCounters* ctr = nullptr;
+  CopySeg* copies = nullptr;
+  WalkSeg* walks = nullptr;
+  unsigned long long* lvl = nullptr;
+  int32_t* orders = nullptr;
+  size_t nslots_meta = 0;
+  std::vector<void*> owned;
+
+  explicit BatchRun(tw_ctx* cc) : c(cc) {}
+  ~BatchRun() {
+    cudaStreamSynchronize(c->stream);
+    for (void* p : {(void*)adj, (void*)akeys, (void*)apar, (void*)table, (void*)okeys, (void*)opar, (void*)segs,
+                    (void*)cbeg, (void*)ctr, (void*)copies, (void*)walks, (void*)lvl, (void*)orders})
+      if (p) cudaFree(p);
+    cudaGetLastError();
+  }
+
+  size_t live_states() const {
+    size_t live = 0;
+    for (const BGraph& x : g)
+      if (x.state == 0)
+        for (const LevelRec& l : x.levels) live += l.count;
+    return live;
+  }
+
+  // Makes room for need more arena states, compacting the live levels of
+  // running graphs into a fresh arena when the current one is full.
+  int arena_room(unsigned long long need) {
+    if (atop + need <= acap) return TW_OK;
+    const unsigned long long live = live_states();
+    const unsigned long long want = std::max<unsigned long long>({acap, 2 * (live + need), 1ull << 20});
+    unsigned long long* nk = nullptr;
+    uint32_t* np = nullptr;
+    int rc = dev_alloc(&nk, want);
+    if (rc == TW_OK) rc = dev_alloc(&np, want);
+    if (rc != TW_OK) {
+      if (nk) cudaFree(nk);
+      return rc;
+    }
+    std::vector<CopySeg> cs;
+    unsigned long long top = 0;
+    for (BGraph& x : g) {
+      if (x.state != 0) continue;
+      for (LevelRec& l : x.levels) {
+        if (l.count) cs.push_back({l.off, top, l.count});
+        l.off = top;
+        top += l.count;
+      }
+    }
+    if (!cs.empty()) {
+      CopySeg* d = nullptr;
+      if ((rc = dev_alloc(&d, cs.size()))) return rc;
+      TW_CK(cudaMemcpyAsync(d, cs.data(), cs.size() * sizeof(CopySeg), cudaMemcpyHostToDevice, c->stream));
+      TW_LAUNCH(c, launch_copy_segments(d, (int)cs.size(), akeys, apar, nk, np, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      cudaFree(d);
+    }
+    TW_CK(cudaStreamSynchronize(c->stream));
+    if (akeys) cudaFree(akeys);
+    if (apar) cudaFree(apar);
+    akeys = nk;
+    apar = np;
+    acap = want;
+    atop = top;
+    return TW_OK;
+  }
+
+  template <class T>
+  int ensure(T** p, unsigned long long* cap, unsigned long long need) {
+    if (need <= *cap && *p) return TW_OK;
+    TW_CK(cudaStreamSynchronize(c->stream));
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    const unsigned long long want = std::max<unsigned long long>(need, *cap * 2);
+    int rc = dev_alloc(p, want);
+    if (rc) return rc;
+    *cap = want;
+    return TW_OK;
+  }
+};
+
+int next_k(const BGraph& x) {
+  if (x.k < 0) return x.k0;
+  if (x.yes_min >= (1 << 30)) return x.no_max + 1;
+  return x.yes_min - 1;
+}
+
+// Records the answer of the run at x.k; returns true when tw is certified
+// (yes at tw and no at tw-1, or tw equal to the lower bound).
+bool record_answer(BGraph& x, bool yes) {
+  if (yes)
+    x.yes_min = std::min(x.yes_min, x.k);
+  else
+    x.no_max = std::max(x.no_max, x.k);
+  if (x.yes_min == x.no_max + 1) {
+    x.tw = x.yes_min;
+    x.state = 1;
+    return true;
+  }
+  return false;
+}
+
+// The batched part: every graph of idx either finishes here (state 1) or is
+// returned in *evicted for the single-graph path.
+int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
+              const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
+              std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st, std::vector<int>* evicted) {
+  BatchRun B(c);
+  const int G = (int)idx.size();
+  if (G == 0) return TW_OK;
+  int rc;
+  // adjacency: 64 rows per graph; bounds input: the same rows
+  {
+    std::vector<unsigned long long> rows((size_t)G * 64, 0ull);
+    std::vector<int32_t> ns(G);
+    std::vector<int64_t> offs(G);
+    for (int j = 0; j < G; ++j) {
+      const HostGraph& hg = graphs[idx[j]];
+      for (int r = 0; r < hg.n; ++r) rows[(size_t)j * 64 + r] = hg.rows[r];
+      ns[j] = hg.n;
+      offs[j] = (int64_t)j * 64;
+    }
+    if ((rc = dev_alloc(&B.adj, rows.size()))) return rc;
+    TW_CK(cudaMemcpyAsync(B.adj, rows.data(), rows.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    int32_t *d_n = nullptr, *d_b = nullptr;
+    int64_t* d_off = nullptr;
+    if ((rc = dev_alloc(&d_n, G)) || (rc = dev_alloc(&d_off, G)) || (rc = dev_alloc(&d_b, (size_t)G * 4))) return rc;
+    TW_CK(cudaMemcpyAsync(d_n, ns.data(), G * 4, cudaMemcpyHostToDevice, c->stream));
+    TW_CK(cudaMemcpyAsync(d_off, offs.data(), G * 8, cudaMemcpyHostToDevice, c->stream));
+    TW_LAUNCH(c, launch_bounds(B.adj, d_n, d_off, G, d_b, nullptr, c->stream));
+    std::vector<int32_t> b((size_t)G * 4);
+    TW_CK(cudaMemcpyAsync(b.data(), d_b, b.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaStreamSynchronize(c->stream));
+    cudaFree(d_n);
+    cudaFree(d_off);
+    cudaFree(d_b);
+    B.g.resize(G);
+    for (int j = 0; j < G; ++j) {
+      BGraph& x = B.g[j];
+      x.in_idx = idx[j];
+      x.n = graphs[idx[j]].n;
+      x.lb = std::max(b[4 * j], b[4 * j + 1]);
+      x.no_max = x.lb - 1;
+      int k0 = x.lb;
+      if (hint) k0 = (int)std::lround((*hint)[idx[j]]);
+      x.k0 = std::min(std::max(k0, x.lb), x.n - 1);
+      x.order_off = order_off[idx[j]];
+    }
+  }
+  int64_t total_n = 0;
+  for (int j = 0; j < G; ++j) total_n = std::max<int64_t>(total_n, B.g[j].order_off + B.g[j].n);
+  if ((rc = dev_alloc(&B.orders, (size_t)total_n))) return rc;
+  if ((rc = dev_alloc(&B.segs, G)) || (rc = dev_alloc(&B.cbeg, (size_t)G + 1)) || (rc = dev_alloc(&B.ctr, G)) ||
+      (rc = dev_alloc(&B.copies, G)) || (rc = dev_alloc(&B.walks, G)) ||
+      (rc = dev_alloc(&B.lvl, (size_t)G * 65)))
+    return rc;
+  std::vector<BatchSeg> segs;
+  std::vector<unsigned long long> cbeg;
+  std::vector<BatchCounters> hc(G);
+  std::vector<CopySeg> copies;
+  std::vector<WalkSeg> walks;
+  std::vector<unsigned long long> lvl;
+  std::vector<int> seg_graph;
+  size_t rr = 0;
+
+  for (int step = 0;; ++step) {
+    // 1. start a run (level 0 = {empty set}) for graphs without one
+    copies.clear();
+    {
+      unsigned long long starting = 0;
+      for (const BGraph& x : B.g)
+        if (x.state == 0 && x.levels.empty()) ++starting;
+      if (starting && (rc = B.arena_room(starting))) return rc;  // before any offset is handed out
+    }
+    for (BGraph& x : B.g) {
+      if (x.state != 0 || !x.levels.empty()) continue;
+      x.k = next_k(x);
+      copies.push_back({~0ull, B.atop, 1});
+      x.levels.push_back({B.atop, 1});
+      B.atop += 1;
+      if (st) st->decide_runs += 1;
+    }
+    if (!copies.empty()) {
+      TW_CK(cudaMemcpyAsync(B.copies, copies.data(), copies.size() * sizeof(CopySeg), cudaMemcpyHostToDevice,
+                            c->stream));
+      TW_LAUNCH(c, launch_copy_segments(B.copies, (int)copies.size(), nullptr, nullptr, B.akeys, B.apar, c->stream));
+    }
+    // 2. finished runs: an empty level answers no; level n-k-1 answers yes
+    walks.clear();
+    lvl.clear();
+    std::vector<int> walked;
+    bool answered = false;
+    for (int j = 0; j < G; ++j) {
+      BGraph& x = B.g[j];
+      if (x.state != 0) continue;
+      const int last = (int)x.levels.size() - 1;
+      if (x.levels.back().count == 0) {
+        record_answer(x, false);
+        x.levels.clear();
+        answered = true;
+      } else if (last == x.n - x.k - 1) {
+        walks.push_back({(unsigned long long)lvl.size(), (unsigned long long)x.order_off, last, x.n});
+        for (const LevelRec& l : x.levels) lvl.push_back(l.off);
+        walked.push_back(j);
+      }
+    }
+    if (!walks.empty()) {
+      TW_CK(cudaMemcpyAsync(B.walks, walks.data(), walks.size() * sizeof(WalkSeg), cudaMemcpyHostToDevice,
+                            c->stream));
+      TW_CK(cudaMemcpyAsync(B.lvl, lvl.data(), lvl.size() * 8, cudaMemcpyHostToDevice, c->stream));
+      TW_LAUNCH(c, launch_walk_batch(B.walks, (int)walks.size(), B.lvl, B.akeys, B.apar, B.orders, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      for (int j : walked) {
+        record_answer(B.g[j], true);
+        B.g[j].levels.clear();
+      }
+      answered = true;
+    }
+    if (answered) continue;  // graphs that answered need their next run started first
+    // 3. build this step's segments (round robin under the step budgets)
+    segs.clear();
+    cbeg.clear();
+    seg_graph.clear();
+    unsigned long long tsum = 0, osum = 0, chunks = 0;
+    int running = 0;
+    for (int t = 0; t < G; ++t) {
+      const int j = (int)((rr + t) % G);
+      BGraph& x = B.g[j];
+      if (x.state != 0) continue;
+      ++running;
+      const int i = (int)x.levels.size() - 1;
+      const LevelRec cur = x.levels.back();
+      const double bound = std::min((double)cur.count * (double)(x.n - i), binom(x.n, i + 1)) + 1.0;
+      double est = x.n;
+      if (i > 0) {
+        const double prev = (double)x.levels[i - 1].count;
+        double r = prev > 0 ? (double)cur.count / prev : 1.0;
+        r = std::min(std::max(r, 0.25), (double)(x.n - i));
+        est = (double)cur.count * r;
+      }
+      const double table_est = std::min(est * 1.25 * x.table_mult + 1024.0, bound);
+      if (est > kEvictStates || (double)x.ocap_retry > kEvictStates) {
+        x.state = 2;
+        x.levels.clear();
+        --running;
+        continue;
+      }
+      const unsigned long long slots = std::max<unsigned long long>(64, (unsigned long long)std::ceil(table_est * 2.0));
+      unsigned long long oc = x.ocap_retry ? x.ocap_retry
+                                           : (unsigned long long)std::ceil(std::min(bound, std::max(table_est * 3.0, 1024.0)));
+      if (!segs.empty() && (tsum + slots > kStepSlots || osum + oc > kStepOut)) continue;
+      BatchSeg sg;
+      sg.in_off = cur.off;
+      sg.in_count = cur.count;
+      sg.t_off = tsum;
+      sg.t_slots = slots;
+      sg.o_off = osum;
+      sg.o_cap = oc;
+      sg.graph = j;
+      sg.n = x.n;
+      sg.k = x.k;
+      sg.pad = 0;
+      segs.push_back(sg);
+      seg_graph.push_back(j);
+      cbeg.push_back(chunks);
+      chunks += (cur.count + 31) / 32;
+      tsum += slots;
+      osum += oc;
+    }
+    rr = (rr + 1) % (size_t)G;
+    if (running == 0) break;
+    if (segs.empty()) continue;  // evictions only
+    cbeg.push_back(chunks);
+    if ((rc = B.ensure(&B.table, &B.tcap, tsum + 2))) return rc;
+    {
+      unsigned long long cap_o = B.ocap;
+      if ((rc = B.ensure(&B.okeys, &cap_o, osum))) return rc;
+      unsigned long long cap_p = B.ocap;
+      if ((rc = B.ensure(&B.opar, &cap_p, osum))) return rc;
+      B.ocap = std::min(cap_o, cap_p);
+    }
+    const int nseg = (int)segs.size();
+    TW_CK(cudaMemcpyAsync(B.segs, segs.data(), nseg * sizeof(BatchSeg), cudaMemcpyHostToDevice, c->stream));
+    TW_CK(cudaMemcpyAsync(B.cbeg, cbeg.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    TW_CK(cudaMemsetAsync(B.ctr, 0, nseg * sizeof(BatchCounters), c->stream));
+    TW_LAUNCH(c, launch_clear(B.table, (size_t)((tsum * 8 + 15) & ~15ull), c->d_ctr, c->stream));
+    TW_LAUNCH(c, launch_expand_batch(B.segs, B.cbeg, nseg, chunks, B.akeys, B.adj, B.table, B.okeys, B.opar, B.ctr,
+                                     kBatchProbes, c->stream));
+    if (st) st->expand_launches += 1;
+    TW_CK(cudaMemcpyAsync(hc.data(), B.ctr, nseg * sizeof(BatchCounters), cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaStreamSynchronize(c->stream));
+    // 4. results: retry, evict or commit into the arena
+    unsigned long long need = 0;
+    for (int s2 = 0; s2 < nseg; ++s2) {
+      BGraph& x = B.g[seg_graph[s2]];
+      const BatchCounters& h = hc[s2];
+      const bool table_full = (h.overflow & 2u) || h.out_count * 100ull > segs[s2].t_slots * 90ull;
+      if (table_full) {
+        x.table_mult *= 2.0;
+        if (st) st->level_retries += 1;
+        continue;
+      }
+      if (h.out_count > segs[s2].o_cap) {
+        x.ocap_retry = h.out_count;
+        if (st) st->level_retries += 1;
+        continue;
+      }
+      need += h.out_count;
+    }
+    if ((rc = B.arena_room(need))) return rc;
+    copies.clear();
+    for (int s2 = 0; s2 < nseg; ++s2) {
+      BGraph& x = B.g[seg_graph[s2]];
+      const BatchCounters& h = hc[s2];
+      const bool table_full = (h.overflow & 2u) || h.out_count * 100ull > segs[s2].t_slots * 90ull;
+      if (table_full || h.out_count > segs[s2].o_cap) continue;
+      x.ocap_retry = 0;
+      const int i = (int)x.levels.size() - 1;
+      if (st) {
+        st->states_expanded += segs[s2].in_count;
+        st->candidates += segs[s2].in_count * (unsigned long long)(x.n - i);
+        st->feasible += h.feasible;
+      }
+      if (h.out_count) copies.push_back({segs[s2].o_off, B.atop, h.out_count});
+      x.levels.push_back({B.atop, h.out_count});
+      B.atop += h.out_count;
+    }
+    if (!copies.empty()) {
+      TW_CK(cudaMemcpyAsync(B.copies, copies.data(), copies.size() * sizeof(CopySeg), cudaMemcpyHostToDevice,
+                            c->stream));
+      TW_LAUNCH(c, launch_copy_segments(B.copies, (int)copies.size(), B.okeys, B.opar, B.akeys, B.apar, c->stream));
+    }
+  }
+  // results of the batched graphs
+  std::vector<int32_t> dord((size_t)total_n);
+  TW_CK(cudaMemcpyAsync(dord.data(), B.orders, dord.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaStreamSynchronize(c->stream));
+  for (BGraph& x : B.g) {
+    if (x.state != 1) continue;
+    htw[x.in_idx] = x.tw;
+    (*hst)[x.in_idx] = TW_OK;
+    if (hord)
+      for (int v = 0; v < x.n; ++v) (*hord)[x.order_off + v] = dord[x.order_off + v];
+  }
+  for (BGraph& x : B.g)
+    if (x.state == 2) evicted->push_back(x.in_idx);
+  return TW_OK;
+}
+
+// Graphs with n <= 64 go through the batched kernel; graphs it evicts and
+// graphs with n > 64 are solved one at a time by the single-graph path.
+int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
+                    const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
+                    std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st) {
+  std::vector<int> small, single;
+  for (int i : idx) (graphs[i].n <= 64 ? small : single).push_back(i);
+  int rc = run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single);
+  if (rc) return rc;
+  for (int gi : single) {
+    const HostGraph& hg = graphs[gi];
+    std::vector<int32_t> ord;
+    int r2;
+    tw_stats local;
+    std::memset(&local, 0, sizeof(local));
+    if (hint) {
+      r2 = solve_hinted(c, hg, (*hint)[gi], &htw[gi], hord ? &ord : nullptr, &local);
+    } else {
+      ord.assign(hg.n, -1);
+      r2 = solve_graph(c, hg, &htw[gi], hord ? ord.data() : nullptr, nullptr, nullptr, &local, 0);
+    }
+    if (st && r2 == TW_OK) {
+      st->states_expanded += local.states_expanded;
+      st->candidates += local.candidates;
+      st->feasible += local.feasible;
+      st->decide_runs += local.decide_runs;
+      st->level_retries += local.level_retries;
+      st->expand_launches += local.expand_launches;
+    }
+    if (r2 == TW_OK && hord)
+      for (int v = 0; v < hg.n; ++v) (*hord)[order_off[gi] + v] = ord[v];
+    if (r2 != TW_OK) htw[gi] = -1;
+    (*hst)[gi] = r2;
+  }
+  return TW_OK;
+}
+
+// Batched per-graph validation into 64-bit rows.
+int load_batch(const uint64_t* adj_concat, const int32_t* n, const int64_t* row_offset, int num_graphs,
+               std::vector<int32_t>* hn, std::vector<int64_t>* hoff, std::vector<uint64_t>* hadj) {
+  if (!adj_concat || !n || !row_offset || num_graphs < 0) return TW_ERR_INVALID;
+  hn->resize(num_graphs);
+  hoff->resize(num_graphs);
+  int rc = fetch(hn->data(), n, (size_t)num_graphs * 4);
+  if (rc) return rc;
+  rc = fetch(hoff->data(), row_offset, (size_t)num_graphs * 8);
+  if (rc) return rc;
+  int64_t words = 0;
+  for (int g = 0; g < num_graphs; ++g) {
+    const int ng = (*hn)[g];
+    if (ng < 1 || ng > TW_MAX_N || (*hoff)[g] < 0) return TW_ERR_INVALID;
+    words = std::max<int64_t>(words, (*hoff)[g] + (int64_t)ng * ((ng + 63) / 64));
+  }
+  hadj->resize((size_t)words);
+  return fetch(hadj->data(), adj_concat, (size_t)words * 8);
+}
+
+}  // namespace host
+}  // namespace tw

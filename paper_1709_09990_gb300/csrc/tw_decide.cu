@@ -1,0 +1,822 @@
+// Host drivers of libtw: decide(k), the k sweep, reconstruction.
+//
+// decide(k) follows Listing 1 of arXiv 1709.09990 (Section 3.1): L_0 = {{}},
+// one expansion per level i = 0 .. n-k-2, stop early at an empty level, and
+// answer yes iff L_{n-k-1} is not empty.  solve() is the iterative deepening
+// of the same section, started at a lower bound instead of 0 (the first yes
+// is the same k).
+//
+// Memory.  Every level's keys and predecessor bytes are kept in one growing
+// device arena when an ordering is wanted (the backward walk reads them);
+// otherwise only the current and the next level are live.  The hash table of
+// the level being built is a second buffer.  Nothing exceeds the context's
+// memory cap: a level that does not fit ends the call with TW_ERR_CAPACITY.
+// A level whose table or output list turns out too small is cleared and run
+// again with larger buffers, so no state is ever lost.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tw_host.h"
+
+namespace tw {
+namespace host {
+
+// Table size above which a level takes the partitioned insert (opt-in: on
+// the heavy levels measured on GB300 the direct kernel, which overlaps its
+// DRAM compare-and-swaps with the search, was 30-40% faster).
+unsigned long long partition_threshold_bytes(const tw_ctx* c) {
+  if (c->cfg.partition_table_mb == -2) return 0ull;
+  if (c->cfg.partition_table_mb <= 0) return ~0ull;
+  return (unsigned long long)c->cfg.partition_table_mb << 20;
+}
+
+// One level through the partitioned insert (emit, then insert range by
+// range), on a cleared table.  *fallback is set when a region overflowed
+// (the caller then runs the direct kernel on a freshly cleared table).
+int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, bool* fallback) {
+  *fallback = false;
+  const size_t w = key_bytes(a.kc);
+  const unsigned long long table_bytes = a.table_slots * w;
+#ifndef TW_PART_SLICE_MB
+#define TW_PART_SLICE_MB 48  // table bytes per hash range: well inside the 126 MB L2
+#endif
+  const int P = (int)std::min<unsigned long long>(
+      kMaxRanges, std::max<unsigned long long>(2, table_bytes / ((unsigned long long)TW_PART_SLICE_MB << 20) + 1));
+  // input chunks whose candidate regions fit a budget of a quarter of the cap
+  const double budget = std::min<double>(16e9, (double)c->mem_cap / 4.0);
+  const double per_state = (double)std::max(1, cand_per_state) * (double)(w + 1);
+  unsigned long long chunk = (unsigned long long)std::max(1024.0, budget / (per_state * 1.2));
+  chunk = std::min<unsigned long long>(chunk, a.n_in);
+  const unsigned long long region_cap =
+      (unsigned long long)std::ceil((double)chunk * std::max(1, cand_per_state) / P * 1.15) + 4096ull;
+  int rc = grow(c, &c->cand_key, (size_t)P * region_cap * w, 0);
+  if (rc == TW_OK) rc = grow(c, &c->cand_v, (size_t)P * region_cap, 0);
+  if (rc == TW_ERR_CAPACITY) {
+    *fallback = true;
+    return TW_OK;
+  }
+  if (rc) return rc;
+  if (!c->part_meta.ptr) {
+    TW_CK(cudaMalloc(&c->part_meta.ptr, 4096));
+    c->part_meta.bytes = 4096;
+  }
+  PartitionBufs pb;
+  pb.ranges = P;
+  pb.cand_key = c->cand_key.ptr;
+  pb.cand_v = static_cast<uint8_t*>(c->cand_v.ptr);
+  pb.region_cap = region_cap;
+  pb.region_cnt = static_cast<unsigned long long*>(c->part_meta.ptr);
+  pb.prefix = pb.region_cnt + kMaxRanges;
+  pb.overflow = reinterpret_cast<unsigned int*>(pb.prefix + kMaxRanges + 1);
+  std::vector<unsigned long long> cnt(P), prefix(P + 1);
+  const size_t kw = key_bytes(a.kc);
+  for (unsigned long long lo = 0; lo < a.n_in; lo += chunk) {
+    ExpandLaunch ca = a;
+    ca.in_keys = static_cast<const char*>(a.in_keys) + lo * kw;
+    ca.n_in = std::min<unsigned long long>(chunk, a.n_in - lo);
+    TW_CK(cudaMemsetAsync(c->part_meta.ptr, 0, 4096, c->stream));
+    TW_LAUNCH(c, launch_emit(ca, pb, c->stream));
+    unsigned int ovf = 0;
+    TW_CK(cudaMemcpyAsync(cnt.data(), pb.region_cnt, P * 8, cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaMemcpyAsync(&ovf, pb.overflow, 4, cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaStreamSynchronize(c->stream));
+    if (ovf) {
+      *fallback = true;
+      return TW_OK;
+    }
+    prefix[0] = 0;
+    for (int r = 0; r < P; ++r) prefix[r + 1] = prefix[r] + std::min(cnt[r], region_cap);
+    TW_CK(cudaMemcpyAsync(pb.prefix, prefix.data(), (P + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    TW_LAUNCH(c, launch_insert_ranges(ca, pb, prefix[P], c->stream));
+  }
+  return TW_OK;
+}
+
+// One run of Listing 1 at bound k on the graph already uploaded.
+int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
+  const size_t w = key_bytes(kc);
+  SmallLayout L;
+  R->levels.clear();
+  R->yes = 0;
+  R->states_expanded = R->candidates = R->feasible = R->peak_bytes = R->retries = 0;
+  R->expand_launches = 0;
+  R->expand_seconds = R->expand_bytes = 0.0;
+  R->fp_sum.assign(1, 0ull);  // fp of the empty set is 0
+  R->fp_xor.assign(1, 0ull);
+  int rc = grow(c, &c->keys, 64 * w, 0);
+  if (rc) return rc;
+  rc = grow(c, &c->pred, 64, 0);
+  if (rc) return rc;
+  TW_CK(cudaMemsetAsync(c->keys.ptr, 0, w, c->stream));
+  R->levels.push_back({0, 1});
+  R->peak_bytes = w + 1;
+  if (k >= n - 1) {
+    R->yes = 1;
+    return TW_OK;
+  }
+  int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  int block_threads = c->cfg.block_threads;
+  const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
+  const bool tune = c->cfg.autotune && c->cfg.table_load_pct == 0 && c->cfg.block_threads == 0;
+  bool tuned_here = false;
+  if (tune)
+    for (const auto& t : c->tuned)
+      if (t.kc == (int)kc && t.nb == n / 8) {
+        load_pct = t.load_pct;
+        block_threads = t.block_threads;
+        tuned_here = true;
+      }
+  unsigned long long kept_states = 1;  // states of kept levels (keep mode)
+  for (int i = 0; i <= n - k - 2; ++i) {
+    const LevelRec cur = R->levels[i];
+    // Upper bounds on |L_{i+1}|: every state has n-i extensions, and there
+    // are C(n, i+1) sets of that size.
+    const double bound = std::min((double)cur.count * (double)(n - i), binom(n, i + 1)) + 1.0;
+    // Prediction from the previous level's growth; the table gets 25% slack
+    // over the prediction at the target load, the output list room for the
+    // worst case (clamped), so output overflow is rare.
+    double est;
+    if (i == 0) {
+      est = n;
+    } else {
+      const double prev = (double)R->levels[i - 1].count;
+      double r = prev > 0 ? (double)cur.count / prev : 1.0;
+      r = std::min(std::max(r, 0.25), (double)(n - i));
+      est = (double)cur.count * r;
+    }
+    double table_est = std::min(est * 1.25 + 1024.0, bound);
+    const double mem_states = (double)c->mem_cap / (double)(w + 1);
+    unsigned long long out_cap =
+        (unsigned long long)std::ceil(std::min(bound, std::max(table_est * 3.0, std::min(bound, mem_states / 4))));
+    unsigned long long slots = std::max<unsigned long long>(
+        64ull, (unsigned long long)std::ceil(table_est * 100.0 / load_pct));
+    // Autotune on the first large level: run it once per candidate
+    // (identical results), keep the fastest choice for this shape.
+    if (tune && !tuned_here && cur.count >= (1ull << 18)) {
+      static const int kBt[2] = {128, 256};
+      static const int kLoad[3] = {40, 50, 60};
+      float best = 1e30f;
+      int best_bt = 128, best_load = 50;
+      for (int bt : kBt)
+        for (int ld : kLoad) {
+          const unsigned long long sl =
+              std::max<unsigned long long>(64ull, (unsigned long long)std::ceil(table_est * 100.0 / ld));
+          const size_t tb = (sl * w + 15) & ~size_t(15);
+          const unsigned long long off = keep_levels ? cur.off + cur.count
+                                                     : ((out_cap <= cur.off) ? 0ull : cur.off + cur.count);
+          rc = grow(c, &c->table, tb, 0);
+          if (rc) return rc;
+          rc = grow(c, &c->keys, (size_t)(off + out_cap) * w, (size_t)(cur.off + cur.count) * w);
+          if (rc) return rc;
+          rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)(cur.off + cur.count));
+          if (rc) return rc;
+          TW_LAUNCH(c, launch_clear(c->table.ptr, tb, c->d_ctr, c->stream));
+          ExpandLaunch a;
+          a.kc = kc;
+          a.in_keys = static_cast<char*>(c->keys.ptr) + cur.off * w;
+          a.n_in = cur.count;
+          a.adj = small_at(c, L.adj);
+          a.n = n;
+          a.k = k;
+          a.table = c->table.ptr;
+          a.table_slots = sl;
+          a.max_probes = max_probes;
+          a.out_keys = static_cast<char*>(c->keys.ptr) + off * w;
+          a.out_pred = static_cast<uint8_t*>(c->pred.ptr) + off;
+          a.out_cap = out_cap;
+          a.ctr = c->d_ctr;
+          a.block_threads = bt;
+          a.grid = 0;
+          a.allowed[0] = c->allowed[0];
+          a.allowed[1] = c->allowed[1];
+          a.mmw = c->cfg.mmw_prune ? 1 : 0;
+          TW_CK(cudaEventRecord(c->ev0, c->stream));
+          TW_LAUNCH(c, launch_expand(a, c->stream));
+          TW_CK(cudaEventRecord(c->ev1, c->stream));
+          TW_CK(cudaStreamSynchronize(c->stream));
+          float ms = 0.f;
+          TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+          if (ms < best) {
+            best = ms;
+            best_bt = bt;
+            best_load = ld;
+          }
+        }
+      c->tuned.push_back({(int)kc, n / 8, best_bt, best_load});
+      load_pct = best_load;
+      block_threads = best_bt;
+      tuned_here = true;
+      slots = std::max<unsigned long long>(64ull, (unsigned long long)std::ceil(table_est * 100.0 / load_pct));
+    }
+    LevelRec nxt;
+    for (int attempt = 0;; ++attempt) {
+      if (attempt > 40) return TW_ERR_CAPACITY;
+      unsigned long long off;
+      if (keep_levels) {
+        off = cur.off + cur.count;
+      } else {
+        off = (out_cap <= cur.off) ? 0ull : cur.off + cur.count;
+      }
+      const unsigned long long live_end = cur.off + cur.count;  // data to keep on growth
+      const size_t table_bytes = (slots * w + 15) & ~size_t(15);
+      rc = grow(c, &c->table, table_bytes, 0);
+      if (rc) return rc;
+      rc = grow(c, &c->keys, (size_t)(off + out_cap) * w, (size_t)live_end * w);
+      if (rc) return rc;
+      rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)live_end);
+      if (rc) return rc;
+      TW_LAUNCH(c, launch_clear(c->table.ptr, table_bytes, c->d_ctr, c->stream));
+      ExpandLaunch a;
+      a.kc = kc;
+      a.in_keys = static_cast<char*>(c->keys.ptr) + cur.off * w;
+      a.n_in = cur.count;
+      a.adj = small_at(c, L.adj);
+      a.n = n;
+      a.k = k;
+      a.table = c->table.ptr;
+      a.table_slots = slots;
+      a.max_probes = max_probes;
+      a.out_keys = static_cast<char*>(c->keys.ptr) + off * w;
+      a.out_pred = static_cast<uint8_t*>(c->pred.ptr) + off;
+      a.out_cap = out_cap;
+      a.ctr = c->d_ctr;
+      a.block_threads = block_threads;
+      a.grid = 0;
+      a.allowed[0] = c->allowed[0];
+      a.allowed[1] = c->allowed[1];
+      a.mmw = c->cfg.mmw_prune ? 1 : 0;
+      const bool timed = c->cfg.time_kernels != 0;
+      if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
+      bool direct = true;
+      if ((unsigned long long)table_bytes > partition_threshold_bytes(c)) {
+        bool fallback = false;
+        rc = run_level_partitioned(c, a, n - c->skipped - i, &fallback);
+        if (rc) return rc;
+        direct = fallback;
+        if (fallback) TW_LAUNCH(c, launch_clear(c->table.ptr, table_bytes, c->d_ctr, c->stream));
+      }
+      if (direct) TW_LAUNCH(c, launch_expand(a, c->stream));
+      if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
+      TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      const LevelCounters h = *c->h_ctr;
+      float ms = 0.f;
+      if (timed) TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      const bool table_full = (h.overflow & 2u) || h.out_count * 100ull > slots * 90ull;
+      if (table_full) {
+        table_est = std::max(table_est * 2.0, (double)h.out_count * 1.5);
+        out_cap = std::max<unsigned long long>(out_cap, (unsigned long long)std::ceil(table_est));
+        slots = (unsigned long long)std::ceil(table_est * 100.0 / load_pct);
+        ++R->retries;
+        continue;
+      }
+      if (h.overflow & 1u) {
+        out_cap = h.out_count;  // exact: every insert that won was counted
+        ++R->retries;
+        continue;
+      }
+      nxt.off = off;
+      nxt.count = h.out_count;
+      R->feasible += h.feasible;
+      R->expand_launches += 1;
+      R->expand_seconds += (double)ms * 1e-3;
+      R->expand_bytes += (double)(cur.count + h.feasible + 2ull * h.out_count) * (double)w + (double)h.out_count;
+      const unsigned long long live_states = keep_levels ? kept_states + nxt.count : cur.count + nxt.count;
+      R->peak_bytes = std::max<unsigned long long>(R->peak_bytes, live_states * (w + 1) + slots * w);
+      break;
+    }
+    R->states_expanded += cur.count;
+    R->candidates += cur.count * (unsigned long long)(n - c->skipped - i);
+    if (keep_levels) kept_states += nxt.count;
+    R->levels.push_back(nxt);
+    if (c->cfg.fingerprints) {
+      TW_LAUNCH(c, launch_fingerprint(kc, static_cast<char*>(c->keys.ptr) + nxt.off * w, nxt.count, c->d_ctr, c->stream));
+      TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      R->fp_sum.push_back(c->h_ctr->fp_sum);
+      R->fp_xor.push_back(c->h_ctr->fp_xor);
+    }
+    if (nxt.count == 0) break;
+  }
+  const int last = (int)R->levels.size() - 1;
+  R->yes = (last == n - k - 1 && R->levels[last].count > 0) ? 1 : 0;
+  return TW_OK;
+}
+
+// decide(k) with the level loop as one captured CUDA graph (every level kept).
+// *bailed is set when the graph gave up (a level did not fit the current
+// buffers or its estimate); the caller then runs the host loop.
+int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool* bailed) {
+  *bailed = true;
+  const int w = (int)key_bytes(kc);
+  if (k >= n - 1) return TW_OK;
+  const unsigned long long arena_cap = std::min<unsigned long long>(c->keys.bytes / w, c->pred.bytes);
+  const unsigned long long table_cap = c->table.bytes >= 16 ? (c->table.bytes - 16) / w : 0;
+  if (arena_cap < 64 || table_cap < 64) return TW_OK;
+  int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  if (c->cfg.autotune && c->cfg.table_load_pct == 0)
+    for (const auto& t : c->tuned)
+      if (t.kc == (int)kc && t.nb == n / 8) load_pct = t.load_pct;
+  const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
+  tw_ctx::GraphEntry* e = nullptr;
+  for (auto& g : c->graphs)
+    if (g.kc == (int)kc && g.n == n && g.k == k && g.load == load_pct && g.probes == max_probes &&
+        g.bt == c->cfg.block_threads && g.allowed0 == c->allowed[0] && g.allowed1 == c->allowed[1] &&
+        g.keys == c->keys.ptr && g.pred == c->pred.ptr && g.table == c->table.ptr && g.arena_cap == arena_cap &&
+        g.table_cap == table_cap)
+      e = &g;
+  if (e == nullptr) {
+    if (c->graphs.size() >= 32) {
+      TW_CK(cudaStreamSynchronize(c->stream));
+      for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+      c->graphs.clear();
+    }
+    SmallLayout L;
+    ExpandLaunch a;
+    a.kc = kc;
+    a.in_keys = c->keys.ptr;
+    a.n_in = 0;
+    a.adj = small_at(c, L.adj);
+    a.n = n;
+    a.k = k;
+    a.table = c->table.ptr;
+    a.table_slots = 0;
+    a.max_probes = max_probes;
+    a.out_keys = c->keys.ptr;
+    a.out_pred = static_cast<uint8_t*>(c->pred.ptr);
+    a.out_cap = 0;
+    a.ctr = c->d_ctr;
+    a.block_threads = 128;
+    a.grid = 0;
+    a.allowed[0] = c->allowed[0];
+    a.allowed[1] = c->allowed[1];
+    a.mmw = c->cfg.mmw_prune ? 1 : 0;
+    cudaGraph_t graph = nullptr;
+    TW_CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    int nodes = 0;
+    cudaError_t err = launch_graph_init(kc, c->d_gstate, c->keys.ptr, c->stream);
+    ++nodes;
+    if (err == cudaSuccess)
+      err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, partition_threshold_bytes(c), n, k,
+                              load_pct, w, 1, c->stream);
+    ++nodes;
+    for (int i = 0; i <= n - k - 2 && err == cudaSuccess; ++i) {
+      err = launch_graph_clear(kc, c->d_gstate, c->table.ptr, c->stream);
+      if (err == cudaSuccess) err = launch_graph_expand(c->d_gstate, a, c->stream);
+      if (err == cudaSuccess)
+        err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, partition_threshold_bytes(c), n, k,
+                                load_pct, w, 0, c->stream);
+      nodes += 3;
+    }
+    const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
+    if (err != cudaSuccess || end != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return TW_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t inst = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TW_CK(inst);
+    c->graphs.push_back({(int)kc, n, k, load_pct, max_probes, c->cfg.block_threads, c->allowed[0], c->allowed[1],
+                         c->keys.ptr, c->pred.ptr, c->table.ptr, arena_cap, table_cap, exec, nodes});
+    e = &c->graphs.back();
+  }
+  TW_CK(cudaGraphLaunch(e->exec, c->stream));
+  c->launches += (unsigned long long)e->nodes;
+  TW_CK(cudaMemcpyAsync(c->h_gstate, c->d_gstate, sizeof(GraphState), cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaStreamSynchronize(c->stream));
+  const GraphState& h = *c->h_gstate;
+  if (h.bail || !h.done) return TW_OK;
+  *bailed = false;
+  R->levels.clear();
+  R->fp_sum.assign(1, 0ull);
+  R->fp_xor.assign(1, 0ull);
+  R->states_expanded = R->candidates = R->retries = 0;
+  R->expand_launches = 0;
+  R->expand_seconds = R->expand_bytes = 0.0;
+  for (int j = 0; j <= h.cur; ++j) R->levels.push_back({h.level_off[j], h.level_cnt[j]});
+  for (int j = 0; j < h.cur; ++j) {
+    R->states_expanded += h.level_cnt[j];
+    R->candidates += h.level_cnt[j] * (unsigned long long)(n - c->skipped - j);
+    R->expand_bytes += (double)(h.level_cnt[j] + 2ull * h.level_cnt[j + 1]) * (double)w + (double)h.level_cnt[j + 1];
+  }
+  R->feasible = h.feasible;
+  R->expand_bytes += (double)h.feasible * (double)w;
+  R->expand_launches = (unsigned long long)h.cur;
+  R->peak_bytes = h.peak_bytes;
+  R->yes = h.yes;
+  if (c->cfg.fingerprints) {
+    for (int j = 1; j <= h.cur; ++j) {
+      TW_CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(LevelCounters), c->stream));
+      TW_LAUNCH(c, launch_fingerprint(kc, static_cast<char*>(c->keys.ptr) + h.level_off[j] * w, h.level_cnt[j],
+                                      c->d_ctr, c->stream));
+      TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      R->fp_sum.push_back(c->h_ctr->fp_sum);
+      R->fp_xor.push_back(c->h_ctr->fp_xor);
+    }
+  }
+  return TW_OK;
+}
+
+// Default of tw_config.graph_levels == 0.
+constexpr bool kGraphLevelsByDefault = true;
+
+bool graph_mode(const tw_ctx* c) {
+  if (c->cfg.time_kernels || c->cfg.graph_levels < 0) return false;
+  return c->cfg.graph_levels > 0 || kGraphLevelsByDefault;
+}
+
+// ---- options of Section 3.1 ------------------------------------------------
+using Set128 = unsigned __int128;
+
+Set128 row_set(const HostGraph& g, int v) {
+  Set128 r = g.rows[(size_t)v * g.words];
+  if (g.words > 1) r |= (Set128)g.rows[(size_t)v * g.words + 1] << 64;
+  return r;
+}
+int popc128(Set128 a) { return __builtin_popcountll((uint64_t)a) + __builtin_popcountll((uint64_t)(a >> 64)); }
+int lowest128(Set128 a) {
+  const uint64_t lo = (uint64_t)a;
+  return lo ? __builtin_ctzll(lo) : 64 + __builtin_ctzll((uint64_t)(a >> 64));
+}
+// Sorted vertex lists compare as: A < B iff the smallest vertex in exactly
+// one of them belongs to A.
+bool lex_less(Set128 a, Set128 b) {
+  const Set128 d = a ^ b;
+  return d != 0 && ((a >> lowest128(d)) & 1);
+}
+
+// Bron-Kerbosch with pivoting over bitsets: every maximal clique is visited,
+// so every maximum one is; the lexicographically smallest maximum is kept.
+void bron_kerbosch(const std::vector<Set128>& nb, Set128 r, Set128 p, Set128 x, int* best_size, Set128* best) {
+  if (p == 0 && x == 0) {
+    const int sz = popc128(r);
+    if (sz > *best_size || (sz == *best_size && lex_less(r, *best))) {
+      *best_size = sz;
+      *best = r;
+    }
+    return;
+  }
+  if (popc128(r) + popc128(p) < *best_size) return;
+  Set128 px = p | x;
+  int pivot = lowest128(px), most = -1;
+  for (Set128 t = px; t; t &= t - 1) {
+    const int u = lowest128(t);
+    const int c = popc128(p & nb[u]);
+    if (c > most) {
+      most = c;
+      pivot = u;
+    }
+  }
+  for (Set128 t = p & ~nb[pivot]; t; t &= t - 1) {
+    const int v = lowest128(t);
+    const Set128 bv = (Set128)1 << v;
+    bron_kerbosch(nb, r | bv, p & nb[v], x & nb[v], best_size, best);
+    p &= ~bv;
+    x |= bv;
+  }
+}
+
+Set128 max_clique(const HostGraph& g) {
+  std::vector<Set128> nb(g.n);
+  for (int v = 0; v < g.n; ++v) nb[v] = row_set(g, v);
+  const Set128 all = g.n == 128 ? ~(Set128)0 : (((Set128)1 << g.n) - 1);
+  int best_size = 0;
+  Set128 best = 0;
+  bron_kerbosch(nb, 0, all, 0, &best_size, &best);
+  return best;
+}
+
+// At least t internally vertex-disjoint u-v paths (u, v not adjacent)?
+// Unit vertex capacities by splitting x into x_in -> x_out; breadth-first
+// augmenting paths in the residual network.
+bool connected_at_least(const HostGraph& g, int u, int v, int t) {
+  const int n = g.n, N = 2 * n;
+  struct Arc {
+    int to, cap, rev;
+  };
+  std::vector<std::vector<Arc>> adj(N);
+  auto add = [&](int a, int b, int cap) {
+    adj[a].push_back({b, cap, (int)adj[b].size()});
+    adj[b].push_back({a, 0, (int)adj[a].size() - 1});
+  };
+  for (int x = 0; x < n; ++x) add(2 * x, 2 * x + 1, (x == u || x == v) ? n : 1);
+  for (int a = 0; a < n; ++a)
+    for (Set128 r = row_set(g, a); r; r &= r - 1) add(2 * a + 1, 2 * lowest128(r), n);
+  const int src = 2 * u + 1, dst = 2 * v;
+  int flow = 0;
+  std::vector<int> pn(N), pa(N);
+  while (flow < t) {
+    std::fill(pn.begin(), pn.end(), -1);
+    std::vector<int> queue{src};
+    pn[src] = src;
+    for (size_t h = 0; h < queue.size() && pn[dst] < 0; ++h) {
+      const int a = queue[h];
+      for (int e = 0; e < (int)adj[a].size(); ++e) {
+        const Arc& arc = adj[a][e];
+        if (arc.cap > 0 && pn[arc.to] < 0) {
+          pn[arc.to] = a;
+          pa[arc.to] = e;
+          queue.push_back(arc.to);
+        }
+      }
+    }
+    if (pn[dst] < 0) break;
+    for (int y = dst; y != src; y = pn[y]) {
+      Arc& arc = adj[pn[y]][pa[y]];
+      arc.cap -= 1;
+      adj[y][arc.rev].cap += 1;
+    }
+    ++flow;
+  }
+  return flow >= t;
+}
+
+// Prepares decide(k) under the context's options: uploads the graph (with
+// the disjoint-path edges for this k) and sets the allowed-vertex mask.
+// *immediate_no is set when the skipped clique alone exceeds k+1 vertices.
+int prepare_options(tw_ctx* c, const HostGraph& g, int k, KeyClass kc, bool* immediate_no) {
+  *immediate_no = false;
+  c->allowed[0] = c->allowed[1] = ~0ull;
+  c->skipped = 0;
+  if (!c->cfg.clique_skip && !c->cfg.disjoint_paths) return TW_OK;
+  HostGraph gk = g;
+  if (c->cfg.disjoint_paths) {
+    for (int u = 0; u < g.n; ++u)
+      for (int v = u + 1; v < g.n; ++v) {
+        if ((row_set(g, u) >> v) & 1) continue;
+        if (!connected_at_least(g, u, v, k + 1)) continue;
+        gk.rows[(size_t)u * g.words + (v >> 6)] |= 1ull << (v & 63);
+        gk.rows[(size_t)v * g.words + (u >> 6)] |= 1ull << (u & 63);
+      }
+  }
+  int rc = upload_graph(c, gk, kc);
+  if (rc) return rc;
+  if (c->cfg.clique_skip) {
+    const Set128 cl = max_clique(g);
+    c->allowed[0] = ~(uint64_t)cl;
+    c->allowed[1] = ~(uint64_t)(cl >> 64);
+    c->skipped = popc128(cl);
+    *immediate_no = c->skipped > k + 1;
+  }
+  return TW_OK;
+}
+
+// The run of a decide answered by the clique bound alone: only L_0.
+void immediate_no_result(DecideResult* R) {
+  R->levels.assign(1, LevelRec{0, 1});
+  R->yes = 0;
+  R->states_expanded = R->candidates = R->feasible = R->retries = 0;
+  R->expand_launches = 0;
+  R->expand_seconds = R->expand_bytes = 0.0;
+  R->peak_bytes = 0;
+  R->fp_sum.assign(1, 0ull);
+  R->fp_xor.assign(1, 0ull);
+}
+
+// decide(k): the graph-driven loop when enabled, else (or when it gives up)
+// the host loop.
+int run_decide_any(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
+  if (graph_mode(c)) {
+    bool bailed = true;
+    int rc = run_decide_graph(c, kc, n, k, R, &bailed);
+    if (rc) return rc;
+    if (!bailed) return TW_OK;
+  }
+  return run_decide(c, kc, n, k, keep_levels, R);
+}
+
+// decide(k) under the context's options (Section 3.1's clique skip and
+// disjoint-path edges when enabled).
+int decide_with_options(tw_ctx* c, const HostGraph& g, KeyClass kc, int k, bool keep_levels, DecideResult* R) {
+  bool no = false;
+  int rc = prepare_options(c, g, k, kc, &no);
+  if (rc) return rc;
+  if (no) {
+    immediate_no_result(R);
+    return TW_OK;
+  }
+  return run_decide_any(c, kc, g.n, k, keep_levels, R);
+}
+
+// Backward walk through the kept levels into the device order buffer.
+int reconstruct(tw_ctx* c, KeyClass kc, int n, const DecideResult& R) {
+  SmallLayout L;
+  const size_t w = key_bytes(kc);
+  const int last = (int)R.levels.size() - 1;
+  int32_t* d_order = reinterpret_cast<int32_t*>(small_at(c, L.order));
+  void* walk = small_at(c, L.walk);
+  char* keys = static_cast<char*>(c->keys.ptr);
+  const uint8_t* pred = static_cast<const uint8_t*>(c->pred.ptr);
+  TW_LAUNCH(c, launch_walk_init(kc, keys + R.levels[last].off * w, walk, last, c->stream));
+  for (int j = last; j >= 1; --j) {
+    const LevelRec& lr = R.levels[j];
+    TW_LAUNCH(c, launch_walk_step(kc, keys + lr.off * w, pred + lr.off, lr.count, walk, j, d_order, c->stream));
+  }
+  TW_LAUNCH(c, launch_walk_finish(kc, walk, last, n, d_order, c->stream));
+  return TW_OK;
+}
+
+void fill_stats(const DecideResult& R, int k, tw_stats* st, bool reset_totals) {
+  if (!st) return;
+  if (reset_totals) {
+    st->states_expanded = st->candidates = st->feasible = st->peak_frontier_bytes = 0;
+    st->decide_runs = st->level_retries = 0;
+    st->expand_launches = 0;
+    st->expand_seconds = st->expand_bytes = 0.0;
+  }
+  st->levels = (int)R.levels.size();
+  st->k = k;
+  for (int i = 0; i <= TW_MAX_N; ++i) {
+    const bool in = i < (int)R.levels.size();
+    st->level_size[i] = in ? R.levels[i].count : 0;
+    st->level_fp_sum[i] = (in && i < (int)R.fp_sum.size()) ? R.fp_sum[i] : 0;
+    st->level_fp_xor[i] = (in && i < (int)R.fp_xor.size()) ? R.fp_xor[i] : 0;
+  }
+  st->states_expanded += R.states_expanded;
+  st->candidates += R.candidates;
+  st->feasible += R.feasible;
+  st->peak_frontier_bytes = std::max<uint64_t>(st->peak_frontier_bytes, R.peak_bytes);
+  st->decide_runs += 1;
+  st->level_retries += R.retries;
+  st->expand_launches += R.expand_launches;
+  st->expand_seconds += R.expand_seconds;
+  st->expand_bytes += R.expand_bytes;
+}
+
+int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order, tw_stats* st) {
+  Timer t;
+  const unsigned long long launches0 = c->launches;
+  if (k < 0 || yes == nullptr) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  const KeyClass kc = key_class_for(g.n);
+  int rc = upload_graph(c, g, kc);
+  if (rc) return rc;
+  DecideResult R;
+  rc = decide_with_options(c, g, kc, k, order != nullptr, &R);
+  if (rc) {
+    // the levels completed before the failure are still reported
+    fill_stats(R, k, st, true);
+    if (st) st->seconds = t.seconds();
+    return rc;
+  }
+  if (R.yes && order) {
+    rc = reconstruct(c, kc, g.n, R);
+    if (rc) return rc;
+    rc = put_from_device(c, order, small_at(c, SmallLayout().order), (size_t)g.n * 4);
+    if (rc) return rc;
+  }
+  TW_CK(cudaStreamSynchronize(c->stream));
+  fill_stats(R, k, st, true);
+  int y = R.yes;
+  rc = put(c, yes, &y, sizeof(int));
+  if (rc) return rc;
+  if (st) {
+    st->seconds = t.seconds();
+    st->kernel_launches = c->launches - launches0;
+  }
+  return TW_OK;
+}
+
+int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]) {
+  SmallLayout L;
+  int32_t* d_out = reinterpret_cast<int32_t*>(small_at(c, L.bounds));
+  int32_t* d_n = d_out + 4;
+  int64_t* d_off = reinterpret_cast<int64_t*>(small_at(c, L.bounds + 64));
+  const int32_t nn = g.n;
+  const int64_t off = 0;
+  TW_CK(cudaMemcpyAsync(d_n, &nn, 4, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(cudaMemcpyAsync(d_off, &off, 8, cudaMemcpyHostToDevice, c->stream));
+  TW_LAUNCH(c, launch_bounds(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), d_n, d_off, 1, d_out,
+                      nullptr, c->stream));
+  TW_CK(cudaMemcpyAsync(out, d_out, 16, cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaStreamSynchronize(c->stream));
+  return TW_OK;
+}
+
+int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int32_t* td_parent, uint64_t* td_bags,
+                tw_stats* st, int k_first) {
+  Timer t;
+  const unsigned long long launches0 = c->launches;
+  TW_CK(cudaSetDevice(c->device));
+  const KeyClass kc = key_class_for(g.n);
+  int rc = upload_graph(c, g, kc);
+  if (rc) return rc;
+  int32_t b[4];
+  rc = bounds_graph(c, g, b);
+  if (rc) return rc;
+  const int lb = std::max(b[0], b[1]);
+  const int ub = std::min(b[2], b[3]);
+  const bool want_walk = order || td_parent || td_bags;
+  if (st) {
+    st->states_expanded = st->candidates = st->feasible = st->peak_frontier_bytes = 0;
+    st->decide_runs = st->level_retries = 0;
+    st->expand_launches = 0;
+    st->expand_seconds = st->expand_bytes = 0.0;
+  }
+  int tw = -1;
+  DecideResult R;
+  int k0 = std::max(lb, k_first);
+  if (c->cfg.ub_shortcut && lb == ub && !want_walk) {
+    tw = ub;
+  } else {
+    for (int k = k0; k < g.n; ++k) {
+      rc = decide_with_options(c, g, kc, k, want_walk, &R);
+      if (rc) return rc;
+      fill_stats(R, k, st, false);
+      if (R.yes) {
+        tw = k;
+        break;
+      }
+    }
+  }
+  if (tw < 0) return TW_ERR_CUDA;
+  if (want_walk && R.yes) {
+    SmallLayout L;
+    rc = reconstruct(c, kc, g.n, R);
+    if (rc) return rc;
+    int32_t* d_order = reinterpret_cast<int32_t*>(small_at(c, L.order));
+    if (c->cfg.disjoint_paths && (rc = upload_graph(c, g, kc))) return rc;  // bags of G itself
+    if (td_parent || td_bags) {
+      TW_LAUNCH(c, launch_td(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), g.n, g.words, d_order,
+                      reinterpret_cast<int32_t*>(small_at(c, L.parent)),
+                      reinterpret_cast<unsigned long long*>(small_at(c, L.bags)), c->stream));
+    }
+    rc = put_from_device(c, order, d_order, (size_t)g.n * 4);
+    if (rc) return rc;
+    rc = put_from_device(c, td_parent, small_at(c, L.parent), (size_t)g.n * 4);
+    if (rc) return rc;
+    rc = put_from_device(c, td_bags, small_at(c, L.bags), (size_t)g.n * g.words * 8);
+    if (rc) return rc;
+  }
+  TW_CK(cudaStreamSynchronize(c->stream));
+  rc = put(c, tw_out, &tw, sizeof(int));
+  if (rc) return rc;
+  if (st) {
+    st->seconds = t.seconds();
+    st->kernel_launches = c->launches - launches0;
+  }
+  return TW_OK;
+}
+
+// Decide runs of one graph guided by a proposed bound: decide(k0) and
+// decide(k0-1) first, then walk up (on no) or down (on yes) until yes at tw
+// and no at tw-1 (or tw = lower bound) certify the answer.  Returns the
+// treewidth in *tw_out and the ordering of the yes run at tw in order_host.
+int solve_hinted(tw_ctx* c, const HostGraph& g, float hint, int* tw_out, std::vector<int32_t>* order_host,
+                 tw_stats* st) {
+  const KeyClass kc = key_class_for(g.n);
+  int rc = upload_graph(c, g, kc);
+  if (rc) return rc;
+  int32_t b[4];
+  if ((rc = bounds_graph(c, g, b))) return rc;
+  const int lb = std::max(b[0], b[1]);
+  int k0 = (int)std::lround(hint);
+  k0 = std::min(std::max(k0, lb), g.n - 1);
+  DecideResult R;
+  SmallLayout L;
+  auto run = [&](int k, int* yes) -> int {
+    int r = decide_with_options(c, g, kc, k, order_host != nullptr, &R);
+    if (r) return r;
+    fill_stats(R, k, st, false);
+    *yes = R.yes;
+    if (R.yes && order_host) {
+      if ((r = reconstruct(c, kc, g.n, R))) return r;
+      order_host->resize(g.n);
+      TW_CK(cudaMemcpyAsync(order_host->data(), small_at(c, L.order), (size_t)g.n * 4, cudaMemcpyDeviceToHost,
+                            c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+    }
+    return TW_OK;
+  };
+  int yes = 0;
+  if ((rc = run(k0, &yes))) return rc;
+  if (yes) {
+    int k = k0;
+    while (k > lb) {
+      int y2 = 0;
+      if ((rc = run(k - 1, &y2))) return rc;
+      if (!y2) break;
+      --k;
+    }
+    *tw_out = k;
+  } else {
+    int k = k0 + 1;
+    for (;; ++k) {
+      int y2 = 0;
+      if ((rc = run(k, &y2))) return rc;
+      if (y2) break;
+    }
+    *tw_out = k;
+  }
+  return TW_OK;
+}
+
+}  // namespace host
+}  // namespace tw
