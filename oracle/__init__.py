@@ -123,9 +123,13 @@ def q_set(adj: Sequence[int], s: int, v: int) -> int:
     return int(out[0]) | (int(out[1]) << 64)
 
 
-def decide(adj: Sequence[int], k: int, want_order: bool = False) -> Dict:
+def decide(adj: Sequence[int], k: int, want_order: bool = False, count_canonical: bool = False) -> Dict:
     """Listing 1 at bound k.  Returns yes, levels, level_size, fp_sum, fp_xor,
-    states_expanded, candidates, feasible and (optionally) order."""
+    states_expanded, candidates, feasible and (optionally) order.  With
+    count_canonical it also returns ``canonical``: the feasible pairs (S, v)
+    whose v lies in the component of G[S u {v}] holding its lowest vertex."""
+    if count_canonical:
+        return decide_opts(adj, k, COUNT_CANONICAL, want_order)
     n = len(adj)
     r = rows(adj)
     ls = np.zeros(n + 1, dtype=np.int64)
@@ -145,7 +149,7 @@ def decide(adj: Sequence[int], k: int, want_order: bool = False) -> Dict:
             "order": order.tolist() if (order is not None and yes) else None}
 
 
-CLIQUE_SKIP, DISJOINT_PATHS, MMW_PRUNE = 1, 2, 4
+CLIQUE_SKIP, DISJOINT_PATHS, MMW_PRUNE, COUNT_CANONICAL = 1, 2, 4, 8
 
 
 def mmw_bound(adj: Sequence[int], s: int = 0) -> int:
@@ -158,14 +162,15 @@ def mmw_bound(adj: Sequence[int], s: int = 0) -> int:
 
 def decide_opts(adj: Sequence[int], k: int, opts: int, want_order: bool = False) -> Dict:
     """decide(k) with the optional reductions of Sections 3.1 and 3.3 (opts:
-    CLIQUE_SKIP, DISJOINT_PATHS, MMW_PRUNE).  Same fields as :func:`decide`."""
+    CLIQUE_SKIP, DISJOINT_PATHS, MMW_PRUNE; COUNT_CANONICAL adds the
+    ``canonical`` counter).  Same fields as :func:`decide`."""
     n = len(adj)
     r = rows(adj)
     ls = np.zeros(n + 1, dtype=np.int64)
     fs = np.zeros(n + 1, dtype=np.uint64)
     fx = np.zeros(n + 1, dtype=np.uint64)
     lv = ctypes.c_int(0)
-    cnt = np.zeros(3, dtype=np.int64)
+    cnt = np.zeros(4, dtype=np.int64)
     order = np.full(n, -1, dtype=np.int32) if want_order else None
     yes = _load().orc_decide_opts(_ptr(r, _u64p), n, k, opts, _ptr(ls, _i64p), _ptr(fs, _u64p), _ptr(fx, _u64p),
                                   ctypes.byref(lv), _ptr(cnt, _i64p),
@@ -175,7 +180,8 @@ def decide_opts(adj: Sequence[int], k: int, opts: int, want_order: bool = False)
     return {"yes": bool(yes), "levels": lv.value, "level_size": ls[: lv.value].tolist(),
             "fp_sum": fs[: lv.value].tolist(), "fp_xor": fx[: lv.value].tolist(),
             "states_expanded": int(cnt[0]), "candidates": int(cnt[1]), "feasible": int(cnt[2]),
-            "order": order.tolist() if (order is not None and yes) else None}
+            "order": order.tolist() if (order is not None and yes) else None,
+            **({"canonical": int(cnt[3])} if opts & COUNT_CANONICAL else {})}
 
 
 def max_clique(adj: Sequence[int]) -> List[int]:

@@ -27,6 +27,12 @@
 //   R4  Sets are exact (the paper's Bloom filter is lossy); level sizes are
 //       the sizes of exact sets.
 //
+// One counter is not part of the paper's method: with COUNT_CANONICAL the
+// decide run also counts the feasible pairs (S, v) whose v lies in the
+// component of G[S u {v}] that holds the lowest vertex of S u {v}.  Those are
+// the pairs the CUDA path submits to its duplicate-removal table; the count is
+// computed here from that definition so the GPU's count can be checked.
+//
 // Independent pins (exercised by tests/test_oracle_*.py):
 //   * brute force over all n! orderings with an explicit elimination game
 //     (remove v, turn its neighbourhood into a clique; Section 2, second
@@ -160,6 +166,30 @@ Key q_set(const Graph& g, const Key& S, int v) {
 
 int popcount_key(const Key& s) { return __builtin_popcountll(s.w[0]) + __builtin_popcountll(s.w[1]); }
 
+int lowest_vertex(const Key& s) { return s.w[0] ? __builtin_ctzll(s.w[0]) : 64 + __builtin_ctzll(s.w[1]); }
+
+// Whether v lies in the component of G[S u {v}] that contains the lowest
+// vertex of S u {v} (a depth-first search from v that stays inside S u {v}).
+bool in_lowest_component(const Graph& g, const Key& S, int v) {
+  const Key T = with(S, v);
+  const int low = lowest_vertex(T);
+  char visited[kMaxN];
+  int stack[kMaxN + 1];
+  std::memset(visited, 0, sizeof(visited));
+  int top = 0;
+  visited[v] = 1;
+  stack[top++] = v;
+  while (top > 0) {
+    const int u = stack[--top];
+    for (int w : g.nbr[u]) {
+      if (visited[w] || !has(T, w)) continue;
+      visited[w] = 1;
+      stack[top++] = w;
+    }
+  }
+  return visited[low] != 0;
+}
+
 struct DecideOut {
   int yes = 0;
   int levels = 0;
@@ -168,6 +198,7 @@ struct DecideOut {
   int64_t states_expanded = 0;
   int64_t candidates = 0;
   int64_t feasible = 0;
+  int64_t canonical = 0;   // counted when asked (see the header)
   std::vector<int> order;  // filled when want_order and yes
 };
 
@@ -178,7 +209,7 @@ int mmw_bound(const Graph& g, const Key& S, int stop_above);
 // mmw_prune, a set whose remaining graph has a minor-min-width bound above k
 // (Section 3.3) is not extended.
 void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::vector<char>* allowed = nullptr,
-            bool mmw_prune = false) {
+            bool mmw_prune = false, bool count_canonical = false) {
   const int n = g.n;
   out->level_size.assign(n + 1, 0);
   out->fp_sum.assign(n + 1, 0);
@@ -210,6 +241,7 @@ void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::v
         const int degree = dfs_degree(g, S, v);
         if (degree <= k) {
           ++out->feasible;
+          if (count_canonical && in_lowest_component(g, S, v)) ++out->canonical;
           outp.emplace(with(S, v), v);  // keeps the first predecessor
         }
       }
@@ -725,7 +757,8 @@ int orc_disjoint_paths(const uint64_t* adj, int n, int u, int v, int limit) {
 // orc_decide with the options of Sections 3.1 and 3.3: bit 0 of opts =
 // clique skip, bit 1 = disjoint-path edges, bit 2 = minor-min-width pruning
 // (on the graph with the added edges).  Same outputs as orc_decide; with the
-// clique skip, candidates count only vertices outside C.
+// clique skip, candidates count only vertices outside C.  Bit 3 counts the
+// canonical pairs (see the header) into counters[3], which must then exist.
 int orc_decide_opts(const uint64_t* adj, int n, int k, int opts, int64_t* level_size, uint64_t* fp_sum,
                     uint64_t* fp_xor, int* levels, int64_t* counters, int32_t* order) {
   Graph g0;
@@ -759,7 +792,7 @@ int orc_decide_opts(const uint64_t* adj, int n, int k, int opts, int64_t* level_
     out.levels = 1;
     out.yes = 0;
   } else {
-    decide(g, k, order != nullptr, &out, filter, (opts & 4) != 0);
+    decide(g, k, order != nullptr, &out, filter, (opts & 4) != 0, (opts & 8) != 0);
   }
   for (int i = 0; i <= n; ++i) {
     if (level_size) level_size[i] = out.level_size[i];
@@ -771,6 +804,7 @@ int orc_decide_opts(const uint64_t* adj, int n, int k, int opts, int64_t* level_
     counters[0] = out.states_expanded;
     counters[1] = out.candidates;
     counters[2] = out.feasible;
+    if (opts & 8) counters[3] = out.canonical;
   }
   if (order && out.yes)
     for (int j = 0; j < n; ++j) order[j] = out.order[j];

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from paper_1709_09990_gb300 import graphgen as gg
+from tests.test_oracle_canonical import _levels
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "tw_oracle.cpp")
 
@@ -29,6 +30,9 @@ MUTANTS = {
     "width_off_by_one": ("width = std::max(width, (int)nb.size());", "width = std::max(width, (int)nb.size() - 1);"),
     "no_stop_at_empty_level": ("    if (inp.empty()) break;  // reading R2\n", ""),
     "fingerprint_constant": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 27)) * 0x94D049BB133111EDULL;"),
+    "canonical_highest_vertex": ("const int low = lowest_vertex(T);",
+                                 "const int low = T.w[1] ? 127 - __builtin_clzll(T.w[1]) : 63 - __builtin_clzll(T.w[0]);"),
+    "canonical_search_leaves_set": ("if (visited[w] || !has(T, w)) continue;", "if (visited[w]) continue;"),
 }
 
 
@@ -50,6 +54,13 @@ def _pins_hold() -> bool:
         assert oracle.solve(gg.cycle(7))["tw"] == 2
         assert oracle.decide(gg.path(8), 1)["level_size"] == [i + 1 for i in range(7)]
         assert oracle.decide([0] * 6, 0)["level_size"] == [math.comb(6, i) for i in range(6)]
+        for s in range(12):
+            rng = gg.Rng(700 + s)
+            n = rng.randint(3, 7)
+            adj = gg.gnp(n, 0.2 + 0.6 * rng.uniform(), 700 + s, rng=rng)
+            for k in range(n):
+                assert oracle.decide(adj, k, count_canonical=True)["canonical"] == _levels(adj, k, True)[1]
+        assert oracle.decide([0] * 6, 0, count_canonical=True)["canonical"] == 2 ** 6 - 2
         # splitmix64's first output from seed 0 (Steele, Lea & Flood 2014)
         assert oracle.fingerprint(0x9E3779B97F4A7C15) == 0xE220A8397B1DCDAF
         return True
