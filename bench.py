@@ -162,7 +162,8 @@ def expand_traffic():
     except (OSError, ValueError):
         return None
     csrc = os.path.join(ROOT, "paper_1709_09990_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("tw_expand.cu", "tw_expand_core.cuh"))
+    src = b"".join(open(os.path.join(csrc, f), "rb").read()
+                   for f in ("tw_expand.cu", "tw_expand_core.cuh", "tw_keys.cuh", "tw_internal.h"))
     if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
     return rec.get("dram_bytes_per_launch")

@@ -42,7 +42,7 @@ extern "C" {
 #endif
 
 #define TW_MAX_N 128
-#define TW_ABI_VERSION 1
+#define TW_ABI_VERSION 2
 
 /* Status codes. */
 #define TW_OK 0
@@ -111,7 +111,12 @@ typedef struct {
   uint64_t states_expanded;                 /* sum of |L_i| over expanded levels,
                                                summed over every decide run    */
   uint64_t candidates;                      /* sum of |L_i| * (n - i), likewise */
-  uint64_t feasible;                        /* candidates with |Q| <= k         */
+  uint64_t generated;                       /* pairs (S, v) with |Q(S, v)| <= k
+                                               submitted to the duplicate-removal
+                                               table: only v in the component of
+                                               G[S u {v}] holding its lowest
+                                               vertex (every such pair with
+                                               mmw_prune), see tw_decide        */
   uint64_t peak_frontier_bytes;             /* max over levels of kept lists +
                                                live table bytes                 */
   uint64_t decide_runs;                     /* decide runs in this call         */
@@ -125,7 +130,7 @@ typedef struct {
                                                sum over levels of (|L_i| + F_i +
                                                2|L_{i+1}|) * w + |L_{i+1}|, with
                                                w the key bytes and F_i the
-                                               feasible candidates             */
+                                               generated pairs of level i      */
 } tw_stats;
 
 /* fp(S) = mix(w0 ^ mix(w1)), mix = the splitmix64 output function, over the
@@ -138,7 +143,10 @@ int tw_create(tw_ctx** out, const tw_config* cfg);
 /* Frees every device buffer of the context.  NULL is ignored. */
 void tw_destroy(tw_ctx* ctx);
 
-/* Listing 1 at bound k (arXiv 1709.09990, Section 3.1).
+/* Listing 1 at bound k (arXiv 1709.09990, Section 3.1).  The level sets are
+ * exactly Listing 1's; each set is generated only from the parents that drop
+ * a vertex of its lowest-vertex component (Q(S, v) depends only on v's
+ * component of G[S u {v}], so no set is lost), which st->generated counts.
  *   adj   : n x ceil(n/64) uint64 rows (see conventions).
  *   k     : the bound, k >= 0.  k >= n-1 answers yes without expansion.
  *   yes   : out, 1 if tw <= k, else 0.

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 6)
     const K S = active ? keys[sg.in_off + idx] : valid;
     const K feas = active ? core::feasible_extensions<K>(S, sAdj[warp], valid, valid, sg.k) : 0ull;
     const int total = core::build_queue<K>(S, feas, lane, sState[warp], sQueue[warp]);
-    if (lane == 0 && total) atomicAdd(&ctr[cur].feasible, (unsigned long long)total);
+    if (lane == 0 && total) atomicAdd(&ctr[cur].generated, (unsigned long long)total);
     out.parent_base = (uint32_t)(local * 32ull);
     core::insert_queue<K, true>(sQueue[warp], sState[warp], total, lane, table + sg.t_off, sg.t_slots, max_probes,
                                 out);

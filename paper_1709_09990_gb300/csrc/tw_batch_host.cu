@@ -388,7 +388,7 @@ int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector
       if (st) {
         st->states_expanded += segs[s2].in_count;
         st->candidates += segs[s2].in_count * (unsigned long long)(x.n - i);
-        st->feasible += h.feasible;
+        st->generated += h.generated;
       }
       if (h.out_count) copies.push_back({segs[s2].o_off, B.atop, h.out_count});
       x.levels.push_back({B.atop, h.out_count});
@@ -440,7 +440,7 @@ int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::
     if (st && r2 == TW_OK) {
       st->states_expanded += local.states_expanded;
       st->candidates += local.candidates;
-      st->feasible += local.feasible;
+      st->generated += local.generated;
       st->decide_runs += local.decide_runs;
       st->level_retries += local.level_retries;
       st->expand_launches += local.expand_launches;

@@ -102,7 +102,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
   SmallLayout L;
   R->levels.clear();
   R->yes = 0;
-  R->states_expanded = R->candidates = R->feasible = R->peak_bytes = R->retries = 0;
+  R->states_expanded = R->candidates = R->generated = R->peak_bytes = R->retries = 0;
   R->expand_launches = 0;
   R->expand_seconds = R->expand_bytes = 0.0;
   R->fp_sum.assign(1, 0ull);  // fp of the empty set is 0
@@ -281,10 +281,10 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       }
       nxt.off = off;
       nxt.count = h.out_count;
-      R->feasible += h.feasible;
+      R->generated += h.generated;
       R->expand_launches += 1;
       R->expand_seconds += (double)ms * 1e-3;
-      R->expand_bytes += (double)(cur.count + h.feasible + 2ull * h.out_count) * (double)w + (double)h.out_count;
+      R->expand_bytes += (double)(cur.count + h.generated + 2ull * h.out_count) * (double)w + (double)h.out_count;
       const unsigned long long live_states = keep_levels ? kept_states + nxt.count : cur.count + nxt.count;
       R->peak_bytes = std::max<unsigned long long>(R->peak_bytes, live_states * (w + 1) + slots * w);
       break;
@@ -405,8 +405,8 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
     R->candidates += h.level_cnt[j] * (unsigned long long)(n - c->skipped - j);
     R->expand_bytes += (double)(h.level_cnt[j] + 2ull * h.level_cnt[j + 1]) * (double)w + (double)h.level_cnt[j + 1];
   }
-  R->feasible = h.feasible;
-  R->expand_bytes += (double)h.feasible * (double)w;
+  R->generated = h.generated;
+  R->expand_bytes += (double)h.generated * (double)w;
   R->expand_launches = (unsigned long long)h.cur;
   R->peak_bytes = h.peak_bytes;
   R->yes = h.yes;
@@ -572,7 +572,7 @@ int prepare_options(tw_ctx* c, const HostGraph& g, int k, KeyClass kc, bool* imm
 void immediate_no_result(DecideResult* R) {
   R->levels.assign(1, LevelRec{0, 1});
   R->yes = 0;
-  R->states_expanded = R->candidates = R->feasible = R->retries = 0;
+  R->states_expanded = R->candidates = R->generated = R->retries = 0;
   R->expand_launches = 0;
   R->expand_seconds = R->expand_bytes = 0.0;
   R->peak_bytes = 0;
@@ -626,7 +626,7 @@ int reconstruct(tw_ctx* c, KeyClass kc, int n, const DecideResult& R) {
 void fill_stats(const DecideResult& R, int k, tw_stats* st, bool reset_totals) {
   if (!st) return;
   if (reset_totals) {
-    st->states_expanded = st->candidates = st->feasible = st->peak_frontier_bytes = 0;
+    st->states_expanded = st->candidates = st->generated = st->peak_frontier_bytes = 0;
     st->decide_runs = st->level_retries = 0;
     st->expand_launches = 0;
     st->expand_seconds = st->expand_bytes = 0.0;
@@ -641,7 +641,7 @@ void fill_stats(const DecideResult& R, int k, tw_stats* st, bool reset_totals) {
   }
   st->states_expanded += R.states_expanded;
   st->candidates += R.candidates;
-  st->feasible += R.feasible;
+  st->generated += R.generated;
   st->peak_frontier_bytes = std::max<uint64_t>(st->peak_frontier_bytes, R.peak_bytes);
   st->decide_runs += 1;
   st->level_retries += R.retries;
@@ -715,7 +715,7 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
   const int ub = std::min(b[2], b[3]);
   const bool want_walk = order || td_parent || td_bags;
   if (st) {
-    st->states_expanded = st->candidates = st->feasible = st->peak_frontier_bytes = 0;
+    st->states_expanded = st->candidates = st->generated = st->peak_frontier_bytes = 0;
     st->decide_runs = st->level_retries = 0;
     st->expand_launches = 0;
     st->expand_seconds = st->expand_bytes = 0.0;

@@ -15,7 +15,10 @@
 //     is reached from v through S exactly when it borders a component of G[S]
 //     that v borders.  Components with |B_C| >= k+2 make every v in B_C
 //     infeasible at once; up to 8 other boundaries stay in registers, and a
-//     state with more falls back to a flood fill per candidate v.
+//     state with more falls back to a flood fill per candidate v.  Only the
+//     canonical candidates are tested: v below min(S), or v on the boundary
+//     of the component of min(S); that generates every set of L_{i+1} (see
+//     feasible_extensions) from about a third as many parents.
 //  2. Warp-cooperative insert: the feasible (S, v) pairs of the 32 states are
 //     packed into a per-warp shared-memory queue, and the whole warp inserts
 //     32 of them at a time with one 4/8/16-byte compare-and-swap each, so

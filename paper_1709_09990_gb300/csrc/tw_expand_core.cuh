@@ -47,7 +47,18 @@ __device__ __forceinline__ unsigned long long home_slot(unsigned long long h, un
 // search of Listing 1.  A boundary with |B_C| >= k+2 rules out all of B_C at
 // once; up to kMaxComps other boundaries stay in registers, and a state with
 // more falls back to a flood fill per candidate.
-template <class K>
+//
+// With kCanonical only the canonical extensions are returned: the v that lie
+// in the component of G[S u {v}] holding the lowest vertex of S u {v}, i.e.
+// v below min(S) or v in the boundary of the component of min(S) (the first
+// one the flood fill finds).  The level sets stay exactly those of Listing 1:
+// Q(S, v) depends only on v's component of G[S u {v}] (a path from v whose
+// interior lies in S never leaves it), so a set is feasible iff each of its
+// components is, and a feasible set T is reached from T \ {u} with u the last
+// vertex of a feasible ordering of T's lowest-vertex component.  Each new set
+// is then produced by far fewer parents, which cuts the candidate tests and
+// the table probes (on the geometric n=40 benchmark graph 3.3x fewer pairs).
+template <class K, bool kCanonical = true>
 __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict__ sAdj, const K valid,
                                                  const K allowed, const int k) {
   K comp_b[kMaxComps];
@@ -58,6 +69,8 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
   K dead = kzero<K>();
   K bordered = kzero<K>();  // union of the kept boundaries
   K rem = S;                // vertices of S not yet in a component
+  K canon = kCanonical ? kbelow_lowest(S) : kones<K>();
+  bool first = true;        // the first component holds min(S)
   while (!kempty(rem)) {
     K todo = klsb(rem);
     rem ^= todo;
@@ -72,6 +85,8 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
       todo |= nw;
     }
     bnd &= ~S;
+    if (kCanonical && first) canon |= bnd;
+    first = false;
     const int bs = kpopc(bnd);
     if (bs >= k + 2) {
       dead |= bnd;
@@ -87,7 +102,7 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
       }
     }
   }
-  K cand = valid & allowed & ~S & ~dead;
+  K cand = valid & allowed & ~S & ~dead & canon;
   K feas = kzero<K>();
   while (!kempty(cand)) {
     const K vb = klsb(cand);
@@ -429,7 +444,7 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   K* sS = sState + warp * 32;
   uint16_t* sQ = sQueue + warp * 32 * kBits;
   const K valid = kfirst_n<K>(p.n);
-  unsigned long long feasible_total = 0;
+  unsigned long long generated_total = 0;
   const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
   const unsigned long long stride = (unsigned long long)gridDim.x * kWarps;
   LevelOut<K, false> out;
@@ -445,14 +460,16 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;
     const K S = active ? p.in_keys[idx] : valid;
-    K feas = active ? feasible_extensions<K>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();
+    // (minor-min-width pruning drops some parents, so it extends by every
+    // feasible vertex)
+    K feas = active ? feasible_extensions<K, !kMMW>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();
     if (kMMW) feas = mmw_filter<K>(S, feas, sAdj, p.n, p.k, lane);
     const int total = build_queue<K>(S, feas, lane, sS, sQ);
-    feasible_total += (unsigned long long)total;
+    generated_total += (unsigned long long)total;
     insert_queue<K, false, U>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out);
     __syncwarp();
   }
-  if (lane == 0 && feasible_total) atomicAdd(&p.ctr->feasible, feasible_total);
+  if (lane == 0 && generated_total) atomicAdd(&p.ctr->generated, generated_total);
 }
 
 }  // namespace core

@@ -29,7 +29,7 @@ __global__ void graph_init_kernel(GraphState* st, K* keys) {
   st->level_off[0] = 0ull;
   st->level_cnt[0] = 1ull;
   st->done = st->bail = st->yes = 0;
-  st->feasible = 0ull;
+  st->generated = 0ull;
   st->peak_bytes = 0ull;
   st->table_slots = st->out_off = st->out_cap = 0ull;
   keys[0] = kzero<K>();  // L_0 = {empty set}
@@ -52,7 +52,7 @@ __global__ void graph_plan_kernel(GraphState* st, LevelCounters* ctr, unsigned l
     st->cur = c;
     st->level_off[c] = st->out_off;
     st->level_cnt[c] = cnt;
-    st->feasible += ctr->feasible;
+    st->generated += ctr->generated;
     const unsigned long long live = st->out_off + cnt;  // every level is kept
     const unsigned long long bytes = live * (unsigned long long)(w + 1) + st->table_slots * (unsigned long long)w;
     if (bytes > st->peak_bytes) st->peak_bytes = bytes;
@@ -92,7 +92,7 @@ __global__ void graph_plan_kernel(GraphState* st, LevelCounters* ctr, unsigned l
   st->out_off = out_off;
   st->out_cap = arena_cap - out_off;
   ctr->out_count = 0ull;
-  ctr->feasible = 0ull;
+  ctr->generated = 0ull;
   ctr->overflow = 0u;
 }
 

@@ -120,7 +120,7 @@ struct LevelRec {
 struct DecideResult {
   int yes = 0;
   std::vector<LevelRec> levels;
-  unsigned long long states_expanded = 0, candidates = 0, feasible = 0, peak_bytes = 0, retries = 0;
+  unsigned long long states_expanded = 0, candidates = 0, generated = 0, peak_bytes = 0, retries = 0;
   unsigned long long expand_launches = 0;
   double expand_seconds = 0.0, expand_bytes = 0.0;
   std::vector<unsigned long long> fp_sum, fp_xor;

@@ -18,7 +18,7 @@ inline size_t key_bytes(KeyClass c) { return c == kKey32 ? 4 : (c == kKey64 ? 8 
 // aligned in device memory and mirrored in pinned host memory).
 struct LevelCounters {
   unsigned long long out_count;  // states appended to L_{i+1} (counts past capacity too)
-  unsigned long long feasible;   // candidates (S, v) with |Q(S, v)| <= k
+  unsigned long long generated;  // pairs (S, v) submitted to the table
   unsigned long long fp_sum;     // sum of fingerprints of L_{i+1}
   unsigned long long fp_xor;     // xor of fingerprints of L_{i+1}
   unsigned int overflow;         // bit 0: output list full, bit 1: probe limit reached
@@ -97,7 +97,7 @@ struct PartitionBufs {
 };
 
 // Launch A: search + per-block counting sort of the pairs into the regions
-// (adds the feasible count to a.ctr).
+// (adds the count of generated pairs to a.ctr).
 cudaError_t launch_emit(const ExpandLaunch& a, const PartitionBufs& pb, cudaStream_t s);
 // Launch B: insert the total region entries range after range into a.table,
 // appending winners to a.out_keys / a.out_pred.
@@ -115,7 +115,7 @@ struct GraphState {
   unsigned long long table_slots;     // table size of the level being built
   unsigned long long out_off;         // arena index where it is written
   unsigned long long out_cap;
-  unsigned long long feasible;        // feasible candidates, summed
+  unsigned long long generated;       // pairs submitted to the table, summed
   unsigned long long peak_bytes;      // max kept-level + table bytes
   int cur;                            // newest level
   int done;
@@ -149,7 +149,7 @@ struct BatchSeg {
 
 struct BatchCounters {
   unsigned long long out_count;
-  unsigned long long feasible;
+  unsigned long long generated;
   unsigned int overflow;  // bit 0: output full, bit 1: probe limit
   unsigned int pad;
   unsigned long long pad2;

@@ -86,6 +86,13 @@ __device__ __forceinline__ K128 klsb(K128 a) {
   return a.lo ? K128{a.lo & (0ull - a.lo), 0ull} : K128{0ull, a.hi & (0ull - a.hi)};
 }
 
+// The vertices below the lowest element of a (every vertex when a is empty).
+__device__ __forceinline__ uint32_t kbelow_lowest(uint32_t a) { return (a - 1u) & ~a; }
+__device__ __forceinline__ unsigned long long kbelow_lowest(unsigned long long a) { return (a - 1ull) & ~a; }
+__device__ __forceinline__ K128 kbelow_lowest(K128 a) {
+  return a.lo ? K128{(a.lo - 1ull) & ~a.lo, 0ull} : K128{~0ull, (a.hi - 1ull) & ~a.hi};
+}
+
 // Index of the only set bit of a one-bit set.
 __device__ __forceinline__ int kindex(uint32_t b) { return 31 - __clz(b); }
 __device__ __forceinline__ int kindex(unsigned long long b) { return 63 - __clzll(b); }

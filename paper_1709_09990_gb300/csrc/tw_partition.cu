@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const K valid = kfirst_n<K>(p.n);
-  unsigned long long feasible_total = 0;
+  unsigned long long generated_total = 0;
   const unsigned long long n_blocks = (p.n_in + kWarps * 32 - 1) / (kWarps * 32);
   for (unsigned long long b = blockIdx.x; b < n_blocks; b += gridDim.x) {
     const unsigned long long idx = b * (kWarps * 32) + warp * 32 + lane;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) start[w + 1] = start[w] + sTotal[w];
     const int T = start[kWarps];
-    feasible_total += (unsigned long long)(threadIdx.x == 0 ? T : 0);
+    generated_total += (unsigned long long)(threadIdx.x == 0 ? T : 0);
     // histogram of the block's pairs over the ranges
     for (int e = threadIdx.x; e < T; e += blockDim.x) {
       int w = 0;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && feasible_total) atomicAdd(&p.ctr->feasible, feasible_total);
+  if (threadIdx.x == 0 && generated_total) atomicAdd(&p.ctr->generated, generated_total);
 }
 
 // Inserts item j of the concatenation of the regions (range-major) for each

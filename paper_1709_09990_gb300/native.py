@@ -45,7 +45,7 @@ class Stats(ctypes.Structure):
                 ("level_fp_sum", ctypes.c_uint64 * (MAX_N + 1)),
                 ("level_fp_xor", ctypes.c_uint64 * (MAX_N + 1)),
                 ("states_expanded", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
-                ("feasible", ctypes.c_uint64), ("peak_frontier_bytes", ctypes.c_uint64),
+                ("generated", ctypes.c_uint64), ("peak_frontier_bytes", ctypes.c_uint64),
                 ("decide_runs", ctypes.c_uint64), ("level_retries", ctypes.c_uint64),
                 ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
                 ("expand_launches", ctypes.c_uint64), ("expand_seconds", ctypes.c_double),
@@ -56,7 +56,7 @@ class Stats(ctypes.Structure):
         return {"levels": L, "k": self.k, "level_size": list(self.level_size[:L]),
                 "fp_sum": list(self.level_fp_sum[:L]), "fp_xor": list(self.level_fp_xor[:L]),
                 "states_expanded": int(self.states_expanded), "candidates": int(self.candidates),
-                "feasible": int(self.feasible), "peak_frontier_bytes": int(self.peak_frontier_bytes),
+                "generated": int(self.generated), "peak_frontier_bytes": int(self.peak_frontier_bytes),
                 "decide_runs": int(self.decide_runs), "level_retries": int(self.level_retries),
                 "seconds": float(self.seconds), "kernel_launches": int(self.kernel_launches),
                 "expand_launches": int(self.expand_launches), "expand_seconds": float(self.expand_seconds),

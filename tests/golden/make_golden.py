@@ -19,11 +19,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def decide_record(adj, k):
-    d = oracle.decide(adj, k)
+    d = oracle.decide(adj, k, count_canonical=True)
     return {"k": k, "yes": d["yes"], "levels": d["levels"], "level_size": d["level_size"],
             "fp_sum": [str(x) for x in d["fp_sum"]], "fp_xor": [str(x) for x in d["fp_xor"]],
             "states_expanded": d["states_expanded"], "candidates": d["candidates"],
-            "feasible": d["feasible"]}
+            "feasible": d["feasible"], "canonical": d["canonical"]}
 
 
 def main():

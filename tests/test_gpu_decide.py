@@ -101,6 +101,7 @@ def test_rgg40_small_k_golden(ctx):
         assert got["yes"] == r["yes"]
         assert got["stats"]["level_size"] == r["level_size"]
         assert [str(x) for x in got["stats"]["fp_sum"]] == r["fp_sum"]
+        assert got["stats"]["generated"] == r["canonical"]
 
 
 def test_rgg40_full_k6_golden(ctx):
@@ -115,6 +116,7 @@ def test_rgg40_full_k6_golden(ctx):
     assert [str(x) for x in got["stats"]["fp_sum"]] == r["fp_sum"]
     assert [str(x) for x in got["stats"]["fp_xor"]] == r["fp_xor"]
     assert got["stats"]["states_expanded"] == r["states_expanded"]
+    assert got["stats"]["generated"] == r["canonical"]
     assert oracle.width_q(adj, got["order"].tolist()) <= 6
 
 
@@ -170,7 +172,7 @@ def test_graph_driven_levels_match_host_loop(case):
             a = host.decide(adj, k=k, want_order=True)
             graph.decide(adj, k=k, want_order=True)  # first call grows the buffers
             b = graph.decide(adj, k=k, want_order=True)
-            for key in ("level_size", "fp_sum", "fp_xor", "states_expanded", "candidates", "feasible", "levels"):
+            for key in ("level_size", "fp_sum", "fp_xor", "states_expanded", "candidates", "generated", "levels"):
                 assert a["stats"][key] == b["stats"][key], (k, key)
             assert a["yes"] == b["yes"]
             if b["yes"]:
