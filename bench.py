@@ -54,6 +54,8 @@ def parse():
                          "learned starting bound vs the plain sweep")
     ap.add_argument("--graphs", type=int, default=0, help="batch/learned: number of graphs (0 = full workload)")
     ap.add_argument("--mem-cap-gb", type=float, default=0.0, help="device memory cap per context (0 = default)")
+    ap.add_argument("--spill-levels", action="store_true",
+                    help="keep finished levels in pinned host memory (tw_config.spill_levels)")
     return ap.parse_args()
 
 
@@ -192,7 +194,8 @@ def run_ours(args):
     order_dev = torch.full((n,), -1, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    ctx = native.Context(device=local, stream=stream.cuda_stream, time_kernels=True)
+    ctx = native.Context(device=local, stream=stream.cuda_stream, time_kernels=True,
+                         spill_levels=args.spill_levels)
 
     def step_device():
         return ctx.solve(rows_dev, n=n, tw_out=tw_dev, order_out=order_dev, want_td=True)
@@ -391,7 +394,7 @@ def run_batch(args):
     N = args.graphs or 4096
     graphs = gg.batch_graphs(N)
     cap = int((args.mem_cap_gb or 16) * (1 << 30))
-    with native.Context(device=0, mem_cap_bytes=cap) as ctx:
+    with native.Context(device=0, mem_cap_bytes=cap, spill_levels=args.spill_levels) as ctx:
         ctx.solve_batch(graphs[:16])
         t = time.perf_counter()
         res = ctx.solve_batch(graphs)
@@ -414,7 +417,7 @@ def run_batch(args):
     _line("time to exact tw, batch", round(tb, 3), "s", args,
           {"workload": f"{N} seeded graphs: even seeds G(n,p), n~U{{16..48}}, p~U[0.1,0.5]; odd seeds partial "
                        "k-trees, k~U{3..12}, 30% edges removed", "graphs": N,
-           "mem_cap_gb": cap / (1 << 30)},
+           "mem_cap_gb": cap / (1 << 30), "spill_levels": bool(args.spill_levels)},
           {"solved": int(ok.sum()), "capacity": int((res["per_graph_status"] == 2).sum()),
            "batch_states_per_s": round(st["states_expanded"] / tb, 1), "loop_seconds": round(tl, 3),
            "loop_states_per_s": round(loop_states / tl, 1), "speedup_vs_loop": round(tl / tb, 3),
@@ -434,7 +437,7 @@ def run_learned(args):
     cap = int((args.mem_cap_gb or 8) * (1 << 30))
     tr = [gg.mixed_graph(10**6 + j, 12, 40, j % 2 == 0) for j in range(ntr)]
     te = [gg.mixed_graph(2 * 10**6 + j, 30, 56, j % 2 == 0) for j in range(nte)]
-    with native.Context(device=0, mem_cap_bytes=cap) as ctx:
+    with native.Context(device=0, mem_cap_bytes=cap, spill_levels=args.spill_levels) as ctx:
         L = learned.label(ctx, tr)
         ok = L["status"] == 0
         # offset chosen on a validation split of the training graphs

@@ -98,6 +98,17 @@ typedef struct {
                              contraction step) above k is not extended.  Answers
                              are unchanged, level sets shrink.  Ignored by
                              tw_solve_batch's batched kernel.                     */
+  int spill_levels;       /* 1 = keep the finished levels, which only the ordering
+                             walk reads, in pinned host memory instead of device
+                             memory: the device then holds just the level being
+                             expanded, the level being built and the table, so
+                             frontiers that would not fit mem_cap_bytes with every
+                             level resident can still be solved (Section 4.2: the
+                             list capacity behind Table 1's starred rows).  Each level
+                             is copied out once on the context's stream; the walk
+                             reads the host copies in place.  Forces the host-
+                             driven level loop.  Results are unchanged.  A failed
+                             host allocation is TW_ERR_CAPACITY.                  */
   int reserved[1];        /* must be zero                                         */
 } tw_config;
 

@@ -127,6 +127,7 @@ void tw_destroy(tw_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (DevBuf* b : {&c->keys, &c->pred, &c->table, &c->small, &c->scratch, &c->cand_key, &c->cand_v, &c->part_meta})
     if (b->ptr) cudaFree(b->ptr);
+  for (const tw_ctx::HostChunk& ch : c->host_chunks) cudaFreeHost(ch.ptr);
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);

@@ -99,6 +99,14 @@ int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, 
 // One run of Listing 1 at bound k on the graph already uploaded.
 int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
   const size_t w = key_bytes(kc);
+  // With spill_levels the finished levels go to pinned host memory and the
+  // device arena only alternates between the input and the output level.
+  const bool spill = keep_levels && c->cfg.spill_levels != 0;
+  if (spill) {
+    c->host_chunk = 0;
+    c->host_used = 0;
+    keep_levels = false;
+  }
   SmallLayout L;
   R->levels.clear();
   R->yes = 0;
@@ -154,6 +162,9 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
         (unsigned long long)std::ceil(std::min(bound, std::max(table_est * 3.0, std::min(bound, mem_states / 4))));
     unsigned long long slots = std::max<unsigned long long>(
         64ull, (unsigned long long)std::ceil(table_est * 100.0 / load_pct));
+    // More than 90% of the slots filled re-runs the level with a larger table,
+    // so the output never needs more room than that.
+    out_cap = std::min(out_cap, slots / 10ull * 9ull + 64ull);
     // Autotune on the first large level: run it once per candidate
     // (identical results), keep the fastest choice for this shape.
     if (tune && !tuned_here && cur.count >= (1ull << 18)) {
@@ -293,6 +304,20 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
     R->candidates += cur.count * (unsigned long long)(n - c->skipped - i);
     if (keep_levels) kept_states += nxt.count;
     R->levels.push_back(nxt);
+    if (spill && nxt.count > 0) {
+      char* hk = nullptr;
+      char* hp = nullptr;
+      rc = host_take(c, (size_t)nxt.count * w, &hk);
+      if (rc) return rc;
+      rc = host_take(c, (size_t)nxt.count, &hp);
+      if (rc) return rc;
+      TW_CK(cudaMemcpyAsync(hk, static_cast<char*>(c->keys.ptr) + nxt.off * w, (size_t)nxt.count * w,
+                            cudaMemcpyDefault, c->stream));
+      TW_CK(cudaMemcpyAsync(hp, static_cast<uint8_t*>(c->pred.ptr) + nxt.off, (size_t)nxt.count, cudaMemcpyDefault,
+                            c->stream));
+      R->levels.back().hkeys = hk;
+      R->levels.back().hpred = reinterpret_cast<const uint8_t*>(hp);
+    }
     if (c->cfg.fingerprints) {
       TW_LAUNCH(c, launch_fingerprint(kc, static_cast<char*>(c->keys.ptr) + nxt.off * w, nxt.count, c->d_ctr, c->stream));
       TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
@@ -428,7 +453,7 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
 constexpr bool kGraphLevelsByDefault = true;
 
 bool graph_mode(const tw_ctx* c) {
-  if (c->cfg.time_kernels || c->cfg.graph_levels < 0) return false;
+  if (c->cfg.time_kernels || c->cfg.spill_levels || c->cfg.graph_levels < 0) return false;
   return c->cfg.graph_levels > 0 || kGraphLevelsByDefault;
 }
 
@@ -614,10 +639,13 @@ int reconstruct(tw_ctx* c, KeyClass kc, int n, const DecideResult& R) {
   void* walk = small_at(c, L.walk);
   char* keys = static_cast<char*>(c->keys.ptr);
   const uint8_t* pred = static_cast<const uint8_t*>(c->pred.ptr);
-  TW_LAUNCH(c, launch_walk_init(kc, keys + R.levels[last].off * w, walk, last, c->stream));
+  // (levels kept in host memory by spill_levels are read there in place)
+  auto level_keys = [&](const LevelRec& lr) -> const char* { return lr.hkeys ? lr.hkeys : keys + lr.off * w; };
+  auto level_pred = [&](const LevelRec& lr) -> const uint8_t* { return lr.hpred ? lr.hpred : pred + lr.off; };
+  TW_LAUNCH(c, launch_walk_init(kc, level_keys(R.levels[last]), walk, last, c->stream));
   for (int j = last; j >= 1; --j) {
     const LevelRec& lr = R.levels[j];
-    TW_LAUNCH(c, launch_walk_step(kc, keys + lr.off * w, pred + lr.off, lr.count, walk, j, d_order, c->stream));
+    TW_LAUNCH(c, launch_walk_step(kc, level_keys(lr), level_pred(lr), lr.count, walk, j, d_order, c->stream));
   }
   TW_LAUNCH(c, launch_walk_finish(kc, walk, last, n, d_order, c->stream));
   return TW_OK;

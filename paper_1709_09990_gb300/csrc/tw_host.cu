@@ -56,6 +56,42 @@ size_t total_bytes(const tw_ctx* c) {
   return c->keys.bytes + c->pred.bytes + c->table.bytes + c->cand_key.bytes + c->cand_v.bytes;
 }
 
+// Takes bytes (rounded up to 256) of pinned, device-mapped host memory from
+// the context's chunks, allocating a chunk of at least kHostChunkBytes when
+// the current ones are full; *out is the device-side address of the bytes.
+// A failed allocation is TW_ERR_CAPACITY.
+int host_take(tw_ctx* c, size_t bytes, char** out) {
+  constexpr size_t kHostChunkBytes = 256ull << 20;
+  bytes = (bytes + 255) & ~size_t(255);
+  while (c->host_chunk < c->host_chunks.size()) {
+    const tw_ctx::HostChunk& ch = c->host_chunks[c->host_chunk];
+    if (c->host_used + bytes <= ch.bytes) {
+      *out = ch.dptr + c->host_used;
+      c->host_used += bytes;
+      return TW_OK;
+    }
+    ++c->host_chunk;
+    c->host_used = 0;
+  }
+  const size_t want = std::max(bytes, kHostChunkBytes);
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, want, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
+    return TW_ERR_CAPACITY;
+  }
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(p);
+    return TW_ERR_CUDA;
+  }
+  c->host_chunks.push_back({static_cast<char*>(p), static_cast<char*>(d), want});
+  c->host_chunk = c->host_chunks.size() - 1;
+  c->host_used = bytes;
+  *out = static_cast<char*>(d);
+  return TW_OK;
+}
+
 // Grows b to at least need bytes, keeping its first keep bytes.  Growth is
 // geometric while the cap allows it.
 int grow(tw_ctx* c, DevBuf* b, size_t need, size_t keep) {

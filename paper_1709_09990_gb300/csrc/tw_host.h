@@ -77,6 +77,15 @@ struct tw_ctx {
     int kc, nb, block_threads, load_pct;
   };
   std::vector<Tuned> tuned;
+  // pinned host chunks that hold finished levels with spill_levels; reused
+  // from the start by every decide run
+  struct HostChunk {
+    char* ptr;   // host address
+    char* dptr;  // device-side address of the same bytes
+    size_t bytes;
+  };
+  std::vector<HostChunk> host_chunks;
+  size_t host_chunk = 0, host_used = 0;  // allocation cursor of the current run
   // options of Section 3.1 for the decide run being prepared
   unsigned long long allowed[2] = {~0ull, ~0ull};
   int skipped = 0;  // vertices excluded from the sets (|C| with the clique skip)
@@ -115,6 +124,8 @@ struct SmallLayout {
 struct LevelRec {
   unsigned long long off = 0;
   unsigned long long count = 0;
+  const char* hkeys = nullptr;     // host copy (spill_levels), else in c->keys at off
+  const uint8_t* hpred = nullptr;  // host copy of the predecessors, else in c->pred
 };
 
 struct DecideResult {
@@ -133,6 +144,7 @@ int put(tw_ctx* c, void* dst, const void* src_host, size_t bytes);
 int put_from_device(tw_ctx* c, void* dst, const void* src_dev, size_t bytes);
 size_t total_bytes(const tw_ctx* c);
 int grow(tw_ctx* c, DevBuf* b, size_t need, size_t keep);
+int host_take(tw_ctx* c, size_t bytes, char** out);
 int validate(const uint64_t* rows, int n, HostGraph* g);
 int load_graph(const uint64_t* adj, int n, HostGraph* g);
 char* small_at(tw_ctx* c, size_t off);

@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
                 ("max_probes", ctypes.c_int), ("ub_shortcut", ctypes.c_int), ("graph_levels", ctypes.c_int),
                 ("time_kernels", ctypes.c_int), ("clique_skip", ctypes.c_int), ("disjoint_paths", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("partition_table_mb", ctypes.c_int), ("mmw_prune", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("spill_levels", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -138,7 +138,7 @@ class Context:
                  stream: int = 0, block_threads: int = 0, table_load_pct: int = 0, max_probes: int = 0,
                  ub_shortcut: bool = False, time_kernels: bool = False, graph_levels: int = 0,
                  autotune: bool = False, clique_skip: bool = False, disjoint_paths: bool = False,
-                 partition_table_mb: int = 0, mmw_prune: bool = False):
+                 partition_table_mb: int = 0, mmw_prune: bool = False, spill_levels: bool = False):
         cfg = Config()
         cfg.device = device
         cfg.fingerprints = int(fingerprints)
@@ -155,6 +155,7 @@ class Context:
         cfg.disjoint_paths = int(disjoint_paths)
         cfg.partition_table_mb = int(partition_table_mb)
         cfg.mmw_prune = int(mmw_prune)
+        cfg.spill_levels = int(spill_levels)
         h = _vp()
         _check(lib().tw_create(ctypes.byref(h), ctypes.byref(cfg)), "tw_create")
         self._h = h
