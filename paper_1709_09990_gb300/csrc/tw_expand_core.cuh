@@ -37,12 +37,86 @@ __device__ __forceinline__ unsigned long long home_slot(unsigned long long h, un
   return __umul64hi(h, slots);
 }
 
+// Floods the component of G[S] that contains the vertices of todo (taken out
+// of rem, the vertices of S not yet in a component) over the adjacency rows in
+// shared memory; returns its outer boundary N(C) \ S and adds the component's
+// vertices to *comp.
+template <class K>
+__device__ __forceinline__ K flood_component(K todo, K& rem, const K S, const K* __restrict__ sAdj, K* comp) {
+  K bnd = kzero<K>();
+  while (!kempty(todo)) {
+    const K b = klsb(todo);
+    todo ^= b;
+    const K r = sAdj[kindex(b)];
+    bnd |= r;
+    const K nw = r & rem;  // unvisited vertices of S next to the component
+    rem ^= nw;
+    todo |= nw;
+    if (comp) *comp |= nw;
+  }
+  return bnd & ~S;
+}
+
+// Adds the boundary of one more component of G[S] to the registers of
+// feasible_extensions: a boundary with |B_C| >= k+2 rules out all of B_C;
+// up to kMaxComps others are kept; beyond that the caller falls back to a
+// flood fill per candidate.
+template <class K>
+__device__ __forceinline__ void keep_boundary(const K bnd, const int k, K (&comp_b)[kMaxComps], int& nc, bool& many,
+                                              K& dead, K& bordered) {
+  const int bs = kpopc(bnd);
+  if (bs >= k + 2) {
+    dead |= bnd;
+  } else if (bs > 0) {
+    if (nc < kMaxComps) {
+#pragma unroll
+      for (int c = 0; c < kMaxComps; ++c)
+        if (c == nc) comp_b[c] = bnd;
+      ++nc;
+      bordered |= bnd;
+    } else {
+      many = true;
+    }
+  }
+}
+
+// |Q(S, v)| <= k for one candidate v (bit vb, row nv = N(v)), given the
+// boundaries of the components of G[S] that v may border.
+template <class K>
+__device__ __forceinline__ bool q_within(const K S, const K vb, const K nv, K q, const K* __restrict__ sAdj,
+                                         const int k, const K (&comp_b)[kMaxComps], const int nc, const bool many,
+                                         const K bordered) {
+  if (!many) {
+    if (!kempty(bordered & vb)) {
+#pragma unroll
+      for (int c = 0; c < kMaxComps; ++c) {
+        if (c >= nc) break;
+        if (!kempty(comp_b[c] & vb)) q |= comp_b[c];
+      }
+    }
+  } else {
+    K vis = nv & S;
+    K front = vis;
+    while (!kempty(front)) {
+      const K b = klsb(front);
+      front ^= b;
+      const K r = sAdj[kindex(b)];
+      q |= r & ~S;
+      const K nw = r & S & ~vis;
+      vis |= nw;
+      front |= nw;
+    }
+  }
+  q &= ~vb;
+  return kpopc(q) <= k;
+}
+
 // The set of vertices v outside S with |Q(S, v)| <= k (thread per state).
 //
 // The components of G[S] are found by a bitset flood fill over the adjacency
-// rows in shared memory (|S| row reads in total); each component C gives its
-// outer boundary B_C = N(C) \ S.  A vertex outside S is reachable from v
-// through S exactly when it borders a component that v borders, so
+// rows in shared memory; each component C gives its outer boundary
+// B_C = N(C) \ S.  A vertex outside S is reachable from v through S exactly
+// when it borders a component that v borders, so
 // Q(S, v) = (N(v) u U{B_C : v in B_C}) \ (S u {v}) - the bitset form of the
 // search of Listing 1.  A boundary with |B_C| >= k+2 rules out all of B_C at
 // once; up to kMaxComps other boundaries stay in registers, and a state with
@@ -50,14 +124,17 @@ __device__ __forceinline__ unsigned long long home_slot(unsigned long long h, un
 //
 // With kCanonical only the canonical extensions are returned: the v that lie
 // in the component of G[S u {v}] holding the lowest vertex of S u {v}, i.e.
-// v below min(S) or v in the boundary of the component of min(S) (the first
-// one the flood fill finds).  The level sets stay exactly those of Listing 1:
-// Q(S, v) depends only on v's component of G[S u {v}] (a path from v whose
-// interior lies in S never leaves it), so a set is feasible iff each of its
-// components is, and a feasible set T is reached from T \ {u} with u the last
-// vertex of a feasible ordering of T's lowest-vertex component.  Each new set
-// is then produced by far fewer parents, which cuts the candidate tests and
-// the table probes (on the geometric n=40 benchmark graph 3.3x fewer pairs).
+// v below min(S) or v in the boundary of the component of min(S).  The level
+// sets stay exactly those of Listing 1: Q(S, v) depends only on v's component
+// of G[S u {v}] (a path from v whose interior lies in S never leaves it), so
+// a set is feasible iff each of its components is, and a feasible set T is
+// reached from T \ {u} with u the last vertex of a feasible ordering of T's
+// lowest-vertex component.  Each new set is then produced by far fewer
+// parents, which cuts the candidate tests and the table probes (on the
+// geometric n=40 benchmark graph 3.3x fewer pairs).  The canonical search is
+// also lazy: it floods the component of min(S) first, which fixes the
+// candidates, and then only the components that border a candidate passing
+// the |N(v) \ S| <= k test.
 template <class K, bool kCanonical = true>
 __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict__ sAdj, const K valid,
                                                  const K allowed, const int k) {
@@ -69,70 +146,60 @@ __device__ __forceinline__ K feasible_extensions(const K S, const K* __restrict_
   K dead = kzero<K>();
   K bordered = kzero<K>();  // union of the kept boundaries
   K rem = S;                // vertices of S not yet in a component
-  K canon = kCanonical ? kbelow_lowest(S) : kones<K>();
-  bool first = true;        // the first component holds min(S)
-  while (!kempty(rem)) {
-    K todo = klsb(rem);
-    rem ^= todo;
-    K bnd = kzero<K>();
-    while (!kempty(todo)) {
-      const K b = klsb(todo);
-      todo ^= b;
-      const K r = sAdj[kindex(b)];
-      bnd |= r;
-      const K nw = r & rem;  // unvisited vertices of S next to the component
-      rem ^= nw;
-      todo |= nw;
+  K cand;
+  if (kCanonical) {
+    K b0 = kzero<K>();  // boundary of the component of min(S)
+    if (!kempty(S)) {
+      const K first = klsb(S);
+      rem ^= first;
+      b0 = flood_component<K>(first, rem, S, sAdj, nullptr);
     }
-    bnd &= ~S;
-    if (kCanonical && first) canon |= bnd;
-    first = false;
-    const int bs = kpopc(bnd);
-    if (bs >= k + 2) {
-      dead |= bnd;
-    } else if (bs > 0) {
-      if (nc < kMaxComps) {
-#pragma unroll
-        for (int c = 0; c < kMaxComps; ++c)
-          if (c == nc) comp_b[c] = bnd;
-        ++nc;
-        bordered |= bnd;
-      } else {
-        many = true;
-      }
+    cand = valid & allowed & ~S & (kbelow_lowest(S) | b0);
+    if (kpopc(b0) >= k + 2) {
+      cand &= ~b0;
+    } else if (!kempty(b0)) {
+      comp_b[0] = b0;
+      nc = 1;
+      bordered = b0;
     }
+    // keep the candidates that pass the cheap test; flood only the
+    // components of S next to them
+    K pre = kzero<K>(), need = kzero<K>();
+    for (K c = cand; !kempty(c);) {
+      const K vb = klsb(c);
+      c ^= vb;
+      const K nv = sAdj[kindex(vb)];
+      if (kpopc(nv & ~S) > k) continue;
+      pre |= vb;
+      need |= nv;
+    }
+    need &= rem;
+    while (!kempty(need)) {
+      const K start = klsb(need);
+      rem ^= start;
+      K comp = start;
+      const K bnd = flood_component<K>(start, rem, S, sAdj, &comp);
+      need &= ~comp;
+      keep_boundary<K>(bnd, k, comp_b, nc, many, dead, bordered);
+    }
+    cand = pre & ~dead;
+  } else {
+    while (!kempty(rem)) {
+      const K start = klsb(rem);
+      rem ^= start;
+      const K bnd = flood_component<K>(start, rem, S, sAdj, nullptr);
+      keep_boundary<K>(bnd, k, comp_b, nc, many, dead, bordered);
+    }
+    cand = valid & allowed & ~S & ~dead;
   }
-  K cand = valid & allowed & ~S & ~dead & canon;
   K feas = kzero<K>();
   while (!kempty(cand)) {
     const K vb = klsb(cand);
     cand ^= vb;
     const K nv = sAdj[kindex(vb)];
-    K q = nv & ~S;
+    const K q = nv & ~S;
     if (kpopc(q) > k) continue;
-    if (!many) {
-      if (!kempty(bordered & vb)) {
-#pragma unroll
-        for (int c = 0; c < kMaxComps; ++c) {
-          if (c >= nc) break;
-          if (!kempty(comp_b[c] & vb)) q |= comp_b[c];
-        }
-      }
-    } else {
-      K vis = nv & S;
-      K front = vis;
-      while (!kempty(front)) {
-        const K b = klsb(front);
-        front ^= b;
-        const K r = sAdj[kindex(b)];
-        q |= r & ~S;
-        const K nw = r & S & ~vis;
-        vis |= nw;
-        front |= nw;
-      }
-    }
-    q &= ~vb;
-    if (kpopc(q) <= k) feas |= vb;
+    if (q_within<K>(S, vb, nv, q, sAdj, k, comp_b, nc, many, bordered)) feas |= vb;
   }
   return feas;
 }
@@ -381,11 +448,11 @@ __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, co
         if (st[u] == 2) {
           const unsigned long long o = b + (unsigned long long)__popc(wm[u] & lanemask_lt);
           if (o < out.cap) {
-            out.keys[o] = key[u];
+            kstore_cs(&out.keys[o], key[u]);
             if (kParent)
-              out.parent[o] = out.parent_base + (uint32_t)src[u];
+              __stcs(&out.parent[o], out.parent_base + (uint32_t)src[u]);
             else
-              out.pred[o] = (uint8_t)vv[u];
+              __stcs(reinterpret_cast<signed char*>(&out.pred[o]), (signed char)vv[u]);
           } else {
             atomicOr(out.overflow, 1u);
           }
@@ -459,7 +526,7 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
        chunk += stride) {
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;
-    const K S = active ? p.in_keys[idx] : valid;
+    const K S = active ? kload_cs(&p.in_keys[idx]) : valid;
     // (minor-min-width pruning drops some parents, so it extends by every
     // feasible vertex)
     K feas = active ? feasible_extensions<K, !kMMW>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();

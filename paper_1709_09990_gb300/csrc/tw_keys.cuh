@@ -169,4 +169,18 @@ __device__ __forceinline__ K128 kload_cg(const K128* p) {
   return {v.x, v.y};
 }
 
+// Streaming (evict-first) load and store for the level lists, which are read
+// or written once per level, so that the hash table keeps the L2.
+__device__ __forceinline__ uint32_t kload_cs(const uint32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ unsigned long long kload_cs(const unsigned long long* p) { return __ldcs(p); }
+__device__ __forceinline__ K128 kload_cs(const K128* p) {
+  const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void kstore_cs(uint32_t* p, uint32_t v) { __stcs(p, v); }
+__device__ __forceinline__ void kstore_cs(unsigned long long* p, unsigned long long v) { __stcs(p, v); }
+__device__ __forceinline__ void kstore_cs(K128* p, K128 v) {
+  __stcs(reinterpret_cast<ulonglong2*>(p), make_ulonglong2(v.lo, v.hi));
+}
+
 }  // namespace tw
