@@ -67,10 +67,12 @@ typedef struct {
   int graph_levels;       /* 1: run each decide's level loop as one captured CUDA
                              graph when the context's buffers can hold it (else
                              the host loop); -1: host-driven loop, one host round
-                             trip per level; 0: the library default.  time_kernels
-                             forces the host loop.                               */
+                             trip per level; 0: the library default.
+                             spill_levels forces the host loop.                  */
   int time_kernels;       /* 1 = time every expand launch with CUDA events on the
-                             context's stream (fills expand_seconds)              */
+                             context's stream (fills expand_seconds); in a
+                             graph-driven level loop the events are event-record
+                             nodes of the graph around each expand launch        */
   int clique_skip;        /* 1 = Section 3.1, first optimisation: a maximum clique
                              C (the one with the lexicographically smallest
                              sorted vertex list) is eliminated last, so decide

@@ -130,7 +130,10 @@ void tw_destroy(tw_ctx* c) {
   for (const tw_ctx::HostChunk& ch : c->host_chunks) cudaFreeHost(ch.ptr);
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
-  for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
+  for (auto& e : c->graphs) {
+    cudaGraphExecDestroy(e.exec);
+    for (cudaEvent_t v : e.ev) cudaEventDestroy(v);
+  }
   if (c->d_gstate) cudaFree(c->d_gstate);
   if (c->h_gstate) cudaFreeHost(c->h_gstate);
   if (c->ev0) cudaEventDestroy(c->ev0);

@@ -347,18 +347,35 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
     for (const auto& t : c->tuned)
       if (t.kc == (int)kc && t.nb == n / 8) load_pct = t.load_pct;
   const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
+  const bool timed = c->cfg.time_kernels != 0;
   tw_ctx::GraphEntry* e = nullptr;
   for (auto& g : c->graphs)
     if (g.kc == (int)kc && g.n == n && g.k == k && g.load == load_pct && g.probes == max_probes &&
         g.bt == c->cfg.block_threads && g.allowed0 == c->allowed[0] && g.allowed1 == c->allowed[1] &&
         g.keys == c->keys.ptr && g.pred == c->pred.ptr && g.table == c->table.ptr && g.arena_cap == arena_cap &&
-        g.table_cap == table_cap)
+        g.table_cap == table_cap && g.ev.empty() == !timed)
       e = &g;
   if (e == nullptr) {
     if (c->graphs.size() >= 32) {
       TW_CK(cudaStreamSynchronize(c->stream));
-      for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+      for (auto& g : c->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        for (cudaEvent_t v : g.ev) cudaEventDestroy(v);
+      }
       c->graphs.clear();
+    }
+    // With time_kernels every level's expand launch is bracketed by two
+    // event-record nodes, read after the replay.
+    std::vector<cudaEvent_t> ev;
+    if (timed) {
+      ev.resize(2 * (size_t)(n - k - 1), nullptr);
+      for (cudaEvent_t& v : ev)
+        if (cudaEventCreate(&v) != cudaSuccess) {
+          cudaGetLastError();
+          for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+          return TW_ERR_CUDA;
+        }
     }
     SmallLayout L;
     ExpandLaunch a;
@@ -391,24 +408,35 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
     ++nodes;
     for (int i = 0; i <= n - k - 2 && err == cudaSuccess; ++i) {
       err = launch_graph_clear(kc, c->d_gstate, c->table.ptr, c->stream);
+      if (err == cudaSuccess && timed) err = cudaEventRecordWithFlags(ev[2 * i], c->stream, cudaEventRecordExternal);
       if (err == cudaSuccess) err = launch_graph_expand(c->d_gstate, a, c->stream);
+      if (err == cudaSuccess && timed)
+        err = cudaEventRecordWithFlags(ev[2 * i + 1], c->stream, cudaEventRecordExternal);
       if (err == cudaSuccess)
         err = launch_graph_plan(c->d_gstate, c->d_ctr, arena_cap, table_cap, partition_threshold_bytes(c), n, k,
                                 load_pct, w, 0, c->stream);
       nodes += 3;
     }
     const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
+    auto drop_events = [&]() {
+      for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    };
     if (err != cudaSuccess || end != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
+      drop_events();
       return TW_ERR_CUDA;
     }
     cudaGraphExec_t exec = nullptr;
     const cudaError_t inst = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
-    TW_CK(inst);
+    if (inst != cudaSuccess) {
+      cudaGetLastError();
+      drop_events();
+      return TW_ERR_CUDA;
+    }
     c->graphs.push_back({(int)kc, n, k, load_pct, max_probes, c->cfg.block_threads, c->allowed[0], c->allowed[1],
-                         c->keys.ptr, c->pred.ptr, c->table.ptr, arena_cap, table_cap, exec, nodes});
+                         c->keys.ptr, c->pred.ptr, c->table.ptr, arena_cap, table_cap, exec, nodes, ev});
     e = &c->graphs.back();
   }
   TW_CK(cudaGraphLaunch(e->exec, c->stream));
@@ -433,6 +461,12 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
   R->generated = h.generated;
   R->expand_bytes += (double)h.generated * (double)w;
   R->expand_launches = (unsigned long long)h.cur;
+  if (!e->ev.empty())
+    for (int j = 0; j < h.cur; ++j) {
+      float ms = 0.f;
+      TW_CK(cudaEventElapsedTime(&ms, e->ev[2 * j], e->ev[2 * j + 1]));
+      R->expand_seconds += (double)ms * 1e-3;
+    }
   R->peak_bytes = h.peak_bytes;
   R->yes = h.yes;
   if (c->cfg.fingerprints) {
@@ -453,7 +487,7 @@ int run_decide_graph(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, bool
 constexpr bool kGraphLevelsByDefault = true;
 
 bool graph_mode(const tw_ctx* c) {
-  if (c->cfg.time_kernels || c->cfg.spill_levels || c->cfg.graph_levels < 0) return false;
+  if (c->cfg.spill_levels || c->cfg.graph_levels < 0) return false;
   return c->cfg.graph_levels > 0 || kGraphLevelsByDefault;
 }
 

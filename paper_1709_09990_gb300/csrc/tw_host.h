@@ -68,6 +68,7 @@ struct tw_ctx {
     unsigned long long arena_cap, table_cap;
     cudaGraphExec_t exec;
     int nodes;
+    std::vector<cudaEvent_t> ev;  // with time_kernels: start and end of every level's expand
   };
   std::vector<GraphEntry> graphs;
   GraphState* d_gstate = nullptr;

@@ -188,3 +188,16 @@ def test_graph_driven_solve_reuses_its_graphs():
         assert r["tw"] == first["tw"] == 8
         assert r["stats"]["states_expanded"] == first["stats"]["states_expanded"]
         assert oracle.verify_td(adj, r["td_parent"], r["td_bags"]) == 8
+
+
+def test_timed_graph_levels_report_expand_time():
+    # time_kernels inside the graph-driven loop (event-record nodes around
+    # every expand) and in the host loop: same levels, both timed
+    adj = gg.workload_rgg40()
+    with context(time_kernels=True, graph_levels=1, fingerprints=True) as a, \
+            context(time_kernels=True, graph_levels=-1, fingerprints=True) as b:
+        a.decide(adj, k=5)  # the first call grows the buffers
+        ra, rb = a.decide(adj, k=5)["stats"], b.decide(adj, k=5)["stats"]
+    for key in ("level_size", "fp_sum", "fp_xor", "generated", "expand_launches"):
+        assert ra[key] == rb[key], key
+    assert ra["expand_seconds"] > 0 and rb["expand_seconds"] > 0
