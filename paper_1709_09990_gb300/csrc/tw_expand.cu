@@ -8,8 +8,9 @@
 //
 // GB300 mapping.  A warp takes 32 consecutive states (coalesced key loads).
 //  1. Thread-per-state: the components of G[S] are found by a bitset flood
-//     fill over the adjacency rows held in shared memory; |S| row reads in
-//     total.  Each component C contributes its outer boundary B_C = N(C) \ S.
+//     fill over the adjacency rows held in shared memory, one row read per
+//     vertex of S at most.  Each component C contributes its outer boundary
+//     B_C = N(C) \ S.
 //     Then Q(S, v) = (N(v) u U{B_C : v in B_C}) \ (S u {v}), the bitset form
 //     of the depth-first search inside Listing 1: a vertex outside S
 //     is reached from v through S exactly when it borders a component of G[S]
@@ -18,7 +19,9 @@
 //     state with more falls back to a flood fill per candidate v.  Only the
 //     canonical candidates are tested: v below min(S), or v on the boundary
 //     of the component of min(S); that generates every set of L_{i+1} (see
-//     feasible_extensions) from about a third as many parents.
+//     feasible_extensions) from about a third as many parents.  The flood
+//     fill is lazy: the component of min(S) first, then only the components
+//     next to a candidate that passes |N(v) \ S| <= k.
 //  2. Warp-cooperative insert: the feasible (S, v) pairs of the 32 states are
 //     packed into a per-warp shared-memory queue, and the whole warp inserts
 //     32 of them at a time with one 4/8/16-byte compare-and-swap each, so

@@ -52,3 +52,34 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
         assert "not built" in str(e)
     else:
         raise AssertionError("expected a loud failure")
+
+
+def _struct_fields(src, name):
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    return re.findall(r"(\w+)\s*(?:\[[^\]]*\])?\s*;", body)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # field names and order of the ctypes mirrors, and every offset and size
+    # as gcc lays the header out on this machine
+    import subprocess
+    from paper_1709_09990_gb300 import native
+    src = open(os.path.join(ROOT, "include", "tw.h")).read()
+    probe = ["#include <stdio.h>", "#include <stddef.h>", '#include "tw.h"', "int main(void) {"]
+    for cname, py in (("tw_config", native.Config), ("tw_stats", native.Stats)):
+        fields = _struct_fields(src, cname)
+        assert fields == [f[0] for f in py._fields_], cname
+        probe.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f in fields:
+            probe.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    probe.append("return 0; }")
+    c = tmp_path / "probe.c"
+    c.write_text("\n".join(probe))
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, py in (("tw_config", native.Config), ("tw_stats", native.Stats)):
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f in _struct_fields(src, cname):
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
