@@ -156,6 +156,20 @@ def peaks():
         return None
 
 
+def kernel_source_hash() -> str:
+    """sha256 of the expand kernel's sources with comments and blank space
+    removed (a comment edit does not change the kernel)."""
+    import re
+    csrc = os.path.join(ROOT, "paper_1709_09990_gb300", "csrc")
+    code = []
+    for f in ("tw_expand.cu", "tw_expand_core.cuh", "tw_keys.cuh", "tw_internal.h"):
+        src = open(os.path.join(csrc, f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        code.append(" ".join(src.split()))
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()
+
+
 def expand_traffic():
     """Per-launch DRAM traffic of the expand kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
@@ -163,10 +177,7 @@ def expand_traffic():
         rec = json.load(open(os.path.join(ROOT, "profiles", "expand_insert_rgg40_traffic.json")))
     except (OSError, ValueError):
         return None
-    csrc = os.path.join(ROOT, "paper_1709_09990_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read()
-                   for f in ("tw_expand.cu", "tw_expand_core.cuh", "tw_keys.cuh", "tw_internal.h"))
-    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    if rec.get("source_sha256") != kernel_source_hash():
         return None
     return rec.get("dram_bytes_per_launch")
 
