@@ -315,8 +315,13 @@ int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector
         continue;
       }
       const unsigned long long slots = std::max<unsigned long long>(64, (unsigned long long)std::ceil(table_est * 2.0));
-      unsigned long long oc = x.ocap_retry ? x.ocap_retry
-                                           : (unsigned long long)std::ceil(std::min(bound, std::max(table_est * 3.0, 1024.0)));
+      // (more than 90% of the slots filled re-runs the level with a larger
+      // table, so the output never needs more room than that)
+      unsigned long long oc =
+          x.ocap_retry ? x.ocap_retry
+                       : std::min<unsigned long long>(
+                             (unsigned long long)std::ceil(std::min(bound, std::max(table_est * 3.0, 1024.0))),
+                             slots / 10ull * 9ull + 64ull);
       if (!segs.empty() && (tsum + slots > kStepSlots || osum + oc > kStepOut)) continue;
       BatchSeg sg;
       sg.in_off = cur.off;
