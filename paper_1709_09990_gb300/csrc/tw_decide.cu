@@ -139,6 +139,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
         tuned_here = true;
       }
   unsigned long long kept_states = 1;  // states of kept levels (keep mode)
+  double gen_per_state = 0.0;          // generated pairs per input state of the last level
   for (int i = 0; i <= n - k - 2; ++i) {
     const LevelRec cur = R->levels[i];
     // Upper bounds on |L_{i+1}|: every state has n-i extensions, and there
@@ -265,7 +266,16 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       bool direct = true;
       if ((unsigned long long)table_bytes > partition_threshold_bytes(c)) {
         bool fallback = false;
-        rc = run_level_partitioned(c, a, n - c->skipped - i, &fallback);
+        // Regions are sized by the pairs per state of the previous level
+        // (with slack), not by the n-i candidates: with canonical parents a
+        // state submits a few pairs, and oversized regions would split the
+        // level into many passes over the table.  A region that still
+        // overflows sends the level to the direct kernel.
+        const int cand_bound = n - c->skipped - i;
+        const int cand_est = gen_per_state > 0.0
+                                 ? std::min(cand_bound, (int)std::ceil(gen_per_state * 2.0) + 2)
+                                 : cand_bound;
+        rc = run_level_partitioned(c, a, cand_est, &fallback);
         if (rc) return rc;
         direct = fallback;
         if (fallback) TW_LAUNCH(c, launch_clear(c->table.ptr, table_bytes, c->d_ctr, c->stream));
@@ -293,6 +303,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       nxt.off = off;
       nxt.count = h.out_count;
       R->generated += h.generated;
+      gen_per_state = cur.count ? (double)h.generated / (double)cur.count : 0.0;
       R->expand_launches += 1;
       R->expand_seconds += (double)ms * 1e-3;
       R->expand_bytes += (double)(cur.count + h.generated + 2ull * h.out_count) * (double)w + (double)h.out_count;
