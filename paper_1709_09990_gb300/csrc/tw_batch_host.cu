@@ -426,6 +426,7 @@ int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector
 int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
                     const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
                     std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st) {
+  NvtxRange range("tw solve_batch graphs=%d", (int)idx.size());
   std::vector<int> small, single;
   for (int i : idx) (graphs[i].n <= 64 ? small : single).push_back(i);
   int rc = run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single);

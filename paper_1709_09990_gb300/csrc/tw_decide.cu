@@ -653,6 +653,7 @@ void immediate_no_result(DecideResult* R) {
 // decide(k): the graph-driven loop when enabled, else (or when it gives up)
 // the host loop.
 int run_decide_any(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
+  NvtxRange range("tw decide n=%d k=%d", n, k);
   if (graph_mode(c)) {
     bool bailed = true;
     int rc = run_decide_graph(c, kc, n, k, R, &bailed);
@@ -677,6 +678,7 @@ int decide_with_options(tw_ctx* c, const HostGraph& g, KeyClass kc, int k, bool 
 
 // Backward walk through the kept levels into the device order buffer.
 int reconstruct(tw_ctx* c, KeyClass kc, int n, const DecideResult& R) {
+  NvtxRange range("tw walk n=%d levels=%d", n, (int)R.levels.size());
   SmallLayout L;
   const size_t w = key_bytes(kc);
   const int last = (int)R.levels.size() - 1;
@@ -775,6 +777,7 @@ int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]) {
 
 int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int32_t* td_parent, uint64_t* td_bags,
                 tw_stats* st, int k_first) {
+  NvtxRange range("tw solve n=%d", g.n);
   Timer t;
   const unsigned long long launches0 = c->launches;
   TW_CK(cudaSetDevice(c->device));

@@ -7,9 +7,12 @@
 
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <chrono>
 #include <cstddef>
 #include <cstdint>
+#include <cstdio>
 #include <vector>
 
 #include "../../include/tw.h"
@@ -96,6 +99,18 @@ namespace tw {
 namespace host {
 
 constexpr size_t kSmallBytes = 1 << 20;
+
+// A named NVTX range for profilers (a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* fmt, int a = 0, int b = 0) {
+    char name[64];
+    std::snprintf(name, sizeof(name), fmt, a, b);
+    nvtxRangePushA(name);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct Timer {
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();

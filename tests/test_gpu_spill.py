@@ -56,3 +56,17 @@ def test_spill_fits_a_cap_the_resident_levels_exceed():
     assert [str(x) for x in got["stats"]["fp_xor"]] == rec["fp_xor"]
     assert got["stats"]["peak_frontier_bytes"] < cap
     assert oracle.width_q(adj, got["order"].tolist()) <= 6
+
+
+def test_batch_with_spilled_levels():
+    # the geometric n=40 graph leaves the batch for the single-graph path,
+    # which keeps its levels in host memory here
+    graphs = [gg.workload_gnp20(), gg.workload_rgg40(), gg.cycle(12), gg.partial_ktree(24, 6, 4)]
+    with context(spill_levels=True) as c:
+        res = c.solve_batch(graphs)
+    assert res["status"] == 0
+    assert res["tw"].tolist() == [8, 6, 2, 6]
+    pos = 0
+    for adj, tw in zip(graphs, res["tw"].tolist()):
+        assert oracle.width_q(adj, res["orders"][pos: pos + len(adj)].tolist()) == tw
+        pos += len(adj)
