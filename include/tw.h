@@ -253,6 +253,11 @@ int tw_mlp_train(tw_ctx* ctx, float* params, const float* x, const float* y, int
  * + 256 bytes inside libtw, held by every GPU that loads the library until
  * the process exits.
  *   d_in_keys  : device, n_in 64-bit keys of level i (bit v = vertex v).
+ *                The output is level i+1 when the input is the whole of
+ *                level i: like tw_decide, each set is extended only by the
+ *                vertices of the component of S u {v} that holds its lowest
+ *                vertex, so from part of a level the output holds just those
+ *                canonical extensions of the given sets.
  *   d_adj      : device, n 64-bit adjacency rows, n <= 64.
  *   k          : the bound.
  *   d_out_keys : device, out_cap keys of level i+1 (written in any order).
