@@ -69,6 +69,9 @@ def _bind(lib):
     lib.orc_disjoint_paths.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.orc_decide_opts.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _u64p, _u64p, _intp,
                                     _i64p, _i32p]
+    if hasattr(lib, "orc_decide_prefix"):
+        lib.orc_decide_prefix.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _u64p, _u64p,
+                                          _i64p]
     return lib
 
 
@@ -147,6 +150,25 @@ def decide(adj: Sequence[int], k: int, want_order: bool = False, count_canonical
             "fp_sum": fs[: lv.value].tolist(), "fp_xor": fx[: lv.value].tolist(),
             "states_expanded": int(cnt[0]), "candidates": int(cnt[1]), "feasible": int(cnt[2]),
             "order": order.tolist() if (order is not None and yes) else None}
+
+
+def decide_prefix(adj: Sequence[int], k: int, max_level: int) -> Dict:
+    """The first levels 0 .. max_level of Listing 1 at bound k (for runs too
+    large to finish here): level_size, fp_sum, fp_xor and the counters of the
+    levels expanded so far, canonical pairs included."""
+    n = len(adj)
+    r = rows(adj)
+    ls = np.zeros(n + 1, dtype=np.int64)
+    fs = np.zeros(n + 1, dtype=np.uint64)
+    fx = np.zeros(n + 1, dtype=np.uint64)
+    cnt = np.zeros(4, dtype=np.int64)
+    lv = _load().orc_decide_prefix(_ptr(r, _u64p), n, k, max_level, _ptr(ls, _i64p), _ptr(fs, _u64p),
+                                   _ptr(fx, _u64p), _ptr(cnt, _i64p))
+    if lv < 0:
+        raise ValueError("invalid graph, k or max_level")
+    return {"levels": lv, "level_size": ls[:lv].tolist(), "fp_sum": fs[:lv].tolist(), "fp_xor": fx[:lv].tolist(),
+            "states_expanded": int(cnt[0]), "candidates": int(cnt[1]), "feasible": int(cnt[2]),
+            "canonical": int(cnt[3])}
 
 
 CLIQUE_SKIP, DISJOINT_PATHS, MMW_PRUNE, COUNT_CANONICAL = 1, 2, 4, 8

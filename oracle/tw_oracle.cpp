@@ -208,8 +208,10 @@ int mmw_bound(const Graph& g, const Key& S, int stop_above);
 // with allowed[v] are added to sets (all of them in the plain method).  With
 // mmw_prune, a set whose remaining graph has a minor-min-width bound above k
 // (Section 3.3) is not extended.
+// With max_level >= 0 the run stops after building level max_level (the
+// first levels of a run too large to finish here; yes is then not decided).
 void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::vector<char>* allowed = nullptr,
-            bool mmw_prune = false, bool count_canonical = false) {
+            bool mmw_prune = false, bool count_canonical = false, int max_level = -1) {
   const int n = g.n;
   out->level_size.assign(n + 1, 0);
   out->fp_sum.assign(n + 1, 0);
@@ -226,7 +228,7 @@ void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::v
   out->fp_xor[0] = out->fp_sum[0];
   int last = 0;
 
-  for (int i = 0; i <= n - k - 2; ++i) {
+  for (int i = 0; i <= n - k - 2 && (max_level < 0 || i < max_level); ++i) {
     std::unordered_map<Key, int, KeyHash> outp;
     for (const auto& entry : inp) {
       const Key& S = entry.first;
@@ -752,6 +754,29 @@ int orc_disjoint_paths(const uint64_t* adj, int n, int u, int v, int limit) {
   Graph g;
   if (!load_graph(adj, n, &g) || u == v || u < 0 || v < 0 || u >= n || v >= n) return -1;
   return disjoint_paths(g, u, v, limit);
+}
+
+// The first levels 0 .. max_level of orc_decide (canonical pairs counted
+// into counters[3]); for runs too large to finish.  Returns the number of
+// levels built, or -1 for invalid input.
+int orc_decide_prefix(const uint64_t* adj, int n, int k, int max_level, int64_t* level_size, uint64_t* fp_sum,
+                      uint64_t* fp_xor, int64_t* counters) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || k < 0 || max_level < 0) return -1;
+  DecideOut out;
+  decide(g, k, false, &out, nullptr, false, true, max_level);
+  for (int i = 0; i <= n; ++i) {
+    if (level_size) level_size[i] = out.level_size[i];
+    if (fp_sum) fp_sum[i] = out.fp_sum[i];
+    if (fp_xor) fp_xor[i] = out.fp_xor[i];
+  }
+  if (counters) {
+    counters[0] = out.states_expanded;
+    counters[1] = out.candidates;
+    counters[2] = out.feasible;
+    counters[3] = out.canonical;
+  }
+  return out.levels;
 }
 
 // orc_decide with the options of Sections 3.1 and 3.3: bit 0 of opts =

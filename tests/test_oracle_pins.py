@@ -172,3 +172,18 @@ def test_fingerprint_is_splitmix64_output():
 def test_fingerprint_distinguishes_words():
     assert oracle.fingerprint(1) != oracle.fingerprint(1 << 64)
     assert oracle.fingerprint(0) == 0
+
+
+def test_decide_prefix_is_the_start_of_decide():
+    # the truncated run builds exactly the first levels of the full run
+    from paper_1709_09990_gb300 import graphgen as gg
+    for adj, k in ((gg.workload_gnp20(), 8), (gg.gnp(14, 0.4, 7), 5), (gg.partial_ktree(16, 4, 1), 4)):
+        full = oracle.decide(adj, k, count_canonical=True)
+        for m in range(0, full["levels"]):
+            p = oracle.decide_prefix(adj, k, m)
+            assert p["levels"] == min(m + 1, full["levels"])
+            for key in ("level_size", "fp_sum", "fp_xor"):
+                assert p[key] == full[key][: p["levels"]], (k, m, key)
+        last = oracle.decide_prefix(adj, k, full["levels"])
+        for key in ("states_expanded", "candidates", "feasible", "canonical"):
+            assert last[key] == full[key], key
