@@ -22,7 +22,8 @@ MUTANTS = {
                              "    for (int w : g.nbr[u]) {\n      if (visited[w]) continue;\n      visited[w] = 1;\n"
                              "      if (has(S, w))\n        stack[top++] = w;\n      else\n        ++degree;"),
     "strict_degree_bound": ("if (degree <= k) {", "if (degree < k) {"),
-    "one_level_short": ("for (int i = 0; i <= n - k - 2; ++i) {", "for (int i = 0; i <= n - k - 3; ++i) {"),
+    "one_level_short": ("for (int i = 0; i <= n - k - 2 && (max_level < 0 || i < max_level); ++i) {",
+                        "for (int i = 0; i <= n - k - 3 && (max_level < 0 || i < max_level); ++i) {"),
     "branches_swapped": ("      if (has(S, w))\n        stack[top++] = w;\n      else\n        ++degree;",
                          "      if (!has(S, w))\n        stack[top++] = w;\n      else\n        ++degree;"),
     "wrong_vertex_added": ("outp.emplace(with(S, v), v);", "outp.emplace(with(S, (v + 1) % n), v);"),
