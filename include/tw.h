@@ -130,8 +130,10 @@ typedef struct {
                                                G[S u {v}] holding its lowest
                                                vertex (every such pair with
                                                mmw_prune), see tw_decide        */
-  uint64_t peak_frontier_bytes;             /* max over levels of kept lists +
-                                               live table bytes                 */
+  uint64_t peak_frontier_bytes;             /* max over levels of the device
+                                               bytes of kept lists + live table
+                                               (levels spilled to host memory
+                                               are not counted)                 */
   uint64_t decide_runs;                     /* decide runs in this call         */
   uint64_t level_retries;                   /* levels re-run after growing      */
   double seconds;                           /* wall time of the call            */
