@@ -34,6 +34,7 @@ MUTANTS = {
     "canonical_highest_vertex": ("const int low = lowest_vertex(T);",
                                  "const int low = T.w[1] ? 127 - __builtin_clzll(T.w[1]) : 63 - __builtin_clzll(T.w[0]);"),
     "canonical_search_leaves_set": ("if (visited[w] || !has(T, w)) continue;", "if (visited[w]) continue;"),
+    "prefix_one_level_short": ("(max_level < 0 || i < max_level)", "(max_level < 0 || i < max_level - 1)"),
 }
 
 
@@ -62,6 +63,10 @@ def _pins_hold() -> bool:
             for k in range(n):
                 assert oracle.decide(adj, k, count_canonical=True)["canonical"] == _levels(adj, k, True)[1]
         assert oracle.decide([0] * 6, 0, count_canonical=True)["canonical"] == 2 ** 6 - 2
+        adj = gg.gnp(12, 0.3, 77)
+        full = oracle.decide(adj, 3)
+        for m in (1, 4):
+            assert oracle.decide_prefix(adj, 3, m)["level_size"] == full["level_size"][: m + 1]
         # splitmix64's first output from seed 0 (Steele, Lea & Flood 2014)
         assert oracle.fingerprint(0x9E3779B97F4A7C15) == 0xE220A8397B1DCDAF
         return True
