@@ -8,13 +8,15 @@ share no code (the seeded input generators in
 method's arithmetic).
 
 Contents:
-  * ``tw_oracle.cpp`` - Listing 1 of van der Zanden & Bodlaender (arXiv
-    1709.09990, Section 3.1) over ``std::unordered_set``-style exact sets,
-    brute force over all orderings, an independent subset DP, ordering and
-    tree-decomposition checks.  Built with g++ by :func:`build`.
+  * ``tw_oracle.cpp`` - the level-by-level test of van der Zanden &
+    Bodlaender (arXiv 1709.09990, Section 3.1) over exact hash sets, with
+    Q(S, v) computed from its Section 2 definition (paths from v whose inner
+    vertices lie in S), brute force over all orderings, an independent subset
+    DP, ordering and tree-decomposition checks.  Built with g++ by
+    :func:`build`.
   * ``bounds.py`` - minimum-degree / minor-min-width lower bounds and
-    min-degree / min-fill upper bounds, and the 12 graph features of the
-    learned starting bound.
+    min-degree / min-fill upper bounds (with their selection sequences), and
+    the 12 graph features of the learned starting bound.
   * ``mlp.py`` - float64 forward/backward/Adam of the 12-32-1 network.
 """
 

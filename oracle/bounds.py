@@ -15,7 +15,9 @@ Upper bounds (widths of greedy elimination orderings):
   * ``min_degree_ub`` - eliminate a minimum-degree vertex each step.
   * ``min_fill_ub`` - eliminate the vertex whose neighbourhood misses the
     fewest edges each step.
-Ties always go to the lowest vertex index.
+Ties always go to the lowest vertex index.  ``mmd_plus_steps``,
+``min_degree_order`` and ``min_fill_order`` return the choices themselves, so
+that tests can pin every selection rule on hand-worked graphs.
 
 Features (12, the input of the learned starting bound), with d(v) the degree:
   0 n/64; 1 edge density 2|E|/(n(n-1)); 2 min d / n; 3 max d / n;
@@ -56,14 +58,18 @@ def mmd(adj: Sequence[int]) -> int:
     return lb
 
 
-def mmd_plus(adj: Sequence[int]) -> int:
+def mmd_plus_steps(adj: Sequence[int]) -> List[tuple]:
+    """The contraction sequence of ``mmd_plus``: one (v, degree of v, u) per
+    step, u = the neighbour v is contracted into (None when v is isolated and
+    simply deleted)."""
     g = _adjsets(adj)
-    lb = 0
+    steps = []
     while len(g) >= 2:
         v = _argmin_degree(g)
-        lb = max(lb, len(g[v]))
+        d = len(g[v])
         if not g[v]:
             del g[v]
+            steps.append((v, 0, None))
             continue
         u = _argmin_degree(g, g[v])
         # contract v into u
@@ -73,7 +79,12 @@ def mmd_plus(adj: Sequence[int]) -> int:
                 g[w].add(u)
                 g[u].add(w)
         del g[v]
-    return lb
+        steps.append((v, d, u))
+    return steps
+
+
+def mmd_plus(adj: Sequence[int]) -> int:
+    return max([d for _, d, _ in mmd_plus_steps(adj)] + [0])
 
 
 def _eliminate(g: Dict[int, Set[int]], v: int) -> int:
@@ -87,13 +98,25 @@ def _eliminate(g: Dict[int, Set[int]], v: int) -> int:
     return len(nb)
 
 
-def min_degree_ub(adj: Sequence[int]) -> int:
+def width_of_order(adj: Sequence[int], order: Sequence[int]) -> int:
+    """Largest degree met when the vertices are eliminated in this order."""
     g = _adjsets(adj)
-    width = 0
+    return max([_eliminate(g, v) for v in order] + [0])
+
+
+def min_degree_order(adj: Sequence[int]) -> List[int]:
+    """Greedy ordering: eliminate a minimum-degree vertex of the current graph."""
+    g = _adjsets(adj)
+    order = []
     while g:
         v = _argmin_degree(g)
-        width = max(width, _eliminate(g, v))
-    return width
+        order.append(v)
+        _eliminate(g, v)
+    return order
+
+
+def min_degree_ub(adj: Sequence[int]) -> int:
+    return width_of_order(adj, min_degree_order(adj))
 
 
 def _fill(g: Dict[int, Set[int]], v: int) -> int:
@@ -106,9 +129,11 @@ def _fill(g: Dict[int, Set[int]], v: int) -> int:
     return missing
 
 
-def min_fill_ub(adj: Sequence[int]) -> int:
+def min_fill_order(adj: Sequence[int]) -> List[int]:
+    """Greedy ordering: eliminate the vertex whose neighbourhood misses the
+    fewest edges in the current graph."""
     g = _adjsets(adj)
-    width = 0
+    order = []
     while g:
         cands = sorted(g)
         best = cands[0]
@@ -117,8 +142,13 @@ def min_fill_ub(adj: Sequence[int]) -> int:
             f = _fill(g, v)
             if f < best_fill:
                 best, best_fill = v, f
-        width = max(width, _eliminate(g, best))
-    return width
+        order.append(best)
+        _eliminate(g, best)
+    return order
+
+
+def min_fill_ub(adj: Sequence[int]) -> int:
+    return width_of_order(adj, min_fill_order(adj))
 
 
 def features(adj: Sequence[int]) -> List[float]:

@@ -5,30 +5,30 @@
 // CPU-baseline leg of the benchmark may load it; the product path never does.
 // It shares no code, header or constant table with the CUDA library.
 //
-// What it follows (van der Zanden & Bodlaender, "Computing Treewidth on the
+// What it computes (van der Zanden & Bodlaender, "Computing Treewidth on the
 // GPU", arXiv 1709.09990):
-//   * Section 2 (Preliminaries): tw(G) = min over orderings pi of
-//     max over v of |Q({u : pi(u) < pi(v)}, v)|, where Q(S, v) is the set of
-//     vertices outside S reachable from v by a path whose interior lies in S.
-//   * Section 3.1, Listing 1: for k = 0, 1, ... start from the list {empty
-//     set}; for levels i = 0 .. n-k-2 extend every set S of the list by every
-//     vertex v not in S whose degree after eliminating S (a depth-first search
-//     over S) is at most k; the union of the extensions is the next list.  A
-//     non-empty list after the last level means tw <= k.  The last k+1
-//     vertices may be eliminated in any order (the third optimisation of
-//     Section 3.1), which is why the level range stops at n-k-1.
+//   * Section 2: for a set S of eliminated vertices and a vertex v outside S,
+//     Q(S, v) is the set of vertices u outside S u {v} for which G has a path
+//     from v to u whose inner vertices all belong to S; |Q(S, v)| is the
+//     degree v has once S has been eliminated.  An ordering's width is the
+//     largest such degree along it, and tw(G) is the smallest width.
+//   * Section 3.1: the treewidth test at bound k keeps, for i = 0, 1, ...,
+//     the family L_i of i-vertex sets that can be eliminated first without a
+//     degree above k.  L_0 holds the empty set, and L_{i+1} is the family of
+//     sets S u {v} with S in L_i, v outside S and |Q(S, v)| <= k.  Since any
+//     k+1 vertices can be eliminated last in any order, tw <= k exactly when
+//     L_{n-k-1} is not empty.  The treewidth is the first k that passes.
 //
 // Readings taken where the paper is silent or ambiguous:
-//   R1  v itself is marked visited before the search starts, so Q(S,v) never
-//       contains v (the definition takes simple paths to u in V \ S).
-//   R2  The listing's level range is canonical; a level that comes out empty
-//       ends the run (every later level would be empty too).
+//   R1  Q(S, v) never contains v itself (the definition speaks of paths to
+//       other vertices; a path that returns to v is not one).
+//   R2  The levels run i = 0 .. n-k-1; an empty level ends the run (every
+//       later level would be empty too) and is the last one reported.
 //   R3  k >= n-1 answers yes with the single level {empty set}.
-//   R4  Sets are exact (the paper's Bloom filter is lossy); level sizes are
-//       the sizes of exact sets.
+//   R4  The families are exact sets (the paper's Bloom filter is lossy).
 //
 // One counter is not part of the paper's method: with COUNT_CANONICAL the
-// decide run also counts the feasible pairs (S, v) whose v lies in the
+// run also counts the pairs (S, v) with |Q(S, v)| <= k whose v lies in the
 // component of G[S u {v}] that holds the lowest vertex of S u {v}.  Those are
 // the pairs the CUDA path submits to its duplicate-removal table; the count is
 // computed here from that definition so the GPU's count can be checked.
@@ -38,7 +38,7 @@
 //     (remove v, turn its neighbourhood into a clique; Section 2, second
 //     paragraph) for n <= 10;
 //   * a subset DP over all 2^n masks that tracks the eliminated graph
-//     explicitly (fill-in edges) instead of the reachability search, n <= 22.
+//     explicitly (fill-in edges) instead of path reachability, n <= 22.
 //
 // Layout of every adjacency argument: n rows of W = ceil(n/64) little-endian
 // uint64 words; bit c of row r is set iff rc is an edge.  n <= 128.
@@ -55,6 +55,7 @@ namespace {
 
 constexpr int kMaxN = 128;
 
+// A vertex set of at most 128 vertices (bit v of word v/64).
 struct Key {
   uint64_t w[2];
   bool operator==(const Key& o) const { return w[0] == o.w[0] && w[1] == o.w[1]; }
@@ -75,6 +76,8 @@ struct KeyHash {
   size_t operator()(const Key& k) const { return (size_t)set_fingerprint(k); }
 };
 
+const Key kNoVertex{{0, 0}};
+
 bool has(const Key& s, int v) { return (s.w[v >> 6] >> (v & 63)) & 1ULL; }
 Key with(Key s, int v) {
   s.w[v >> 6] |= 1ULL << (v & 63);
@@ -84,21 +87,41 @@ Key without(Key s, int v) {
   s.w[v >> 6] &= ~(1ULL << (v & 63));
   return s;
 }
+Key set_union(const Key& a, const Key& b) { return Key{{a.w[0] | b.w[0], a.w[1] | b.w[1]}}; }
+Key set_meet(const Key& a, const Key& b) { return Key{{a.w[0] & b.w[0], a.w[1] & b.w[1]}}; }
+Key set_minus(const Key& a, const Key& b) { return Key{{a.w[0] & ~b.w[0], a.w[1] & ~b.w[1]}}; }
+bool is_empty(const Key& s) { return (s.w[0] | s.w[1]) == 0; }
+
+int popcount_key(const Key& s) { return __builtin_popcountll(s.w[0]) + __builtin_popcountll(s.w[1]); }
+
+int lowest_vertex(const Key& s) { return s.w[0] ? __builtin_ctzll(s.w[0]) : 64 + __builtin_ctzll(s.w[1]); }
 
 struct Graph {
   int n = 0;
   std::vector<std::vector<int>> nbr;        // adjacency lists, increasing order
   std::vector<std::vector<char>> mat;       // adjacency matrix
+  std::vector<Key> nset;                    // N(v) as a vertex set
 };
 
 int words_for(int n) { return n <= 64 ? 1 : (n + 63) / 64; }
+
+// Rebuilds the adjacency lists and neighbour sets from the matrix.
+void derive_lists(Graph* g) {
+  g->nbr.assign(g->n, {});
+  g->nset.assign(g->n, kNoVertex);
+  for (int r = 0; r < g->n; ++r)
+    for (int c = 0; c < g->n; ++c)
+      if (g->mat[r][c]) {
+        g->nbr[r].push_back(c);
+        g->nset[r] = with(g->nset[r], c);
+      }
+}
 
 // Returns false on an invalid graph (asymmetric row, self-loop, bits >= n).
 bool load_graph(const uint64_t* adj, int n, Graph* g) {
   if (n < 1 || n > kMaxN || adj == nullptr) return false;
   const int W = words_for(n);
   g->n = n;
-  g->nbr.assign(n, {});
   g->mat.assign(n, std::vector<char>(n, 0));
   for (int r = 0; r < n; ++r) {
     for (int c = 0; c < W * 64; ++c) {
@@ -109,85 +132,51 @@ bool load_graph(const uint64_t* adj, int n, Graph* g) {
     }
   }
   for (int r = 0; r < n; ++r)
-    for (int c = 0; c < n; ++c) {
+    for (int c = 0; c < n; ++c)
       if (g->mat[r][c] != g->mat[c][r]) return false;
-      if (g->mat[r][c]) g->nbr[r].push_back(c);
-    }
+  derive_lists(g);
   return true;
 }
 
-// Listing 1, the inner search: the degree of v in the graph that remains after
-// eliminating S, found by a depth-first search from v through S.  Every
-// first-time-seen vertex outside S adds one.  Reading R1: v starts visited.
-int dfs_degree(const Graph& g, const Key& S, int v) {
-  char visited[kMaxN];
-  int stack[kMaxN + 1];
-  std::memset(visited, 0, sizeof(visited));
-  int top = 0;
-  int degree = 0;
-  visited[v] = 1;
-  stack[top++] = v;
-  while (top > 0) {
-    const int u = stack[--top];
-    for (int w : g.nbr[u]) {
-      if (visited[w]) continue;
-      visited[w] = 1;
-      if (has(S, w))
-        stack[top++] = w;
-      else
-        ++degree;
-    }
-  }
-  return degree;
+// The union of N(x) over the vertices x of X.
+Key neighbours_of(const Graph& g, const Key& X) {
+  Key out = kNoVertex;
+  for (int x = 0; x < g.n; ++x)
+    if (has(X, x)) out = set_union(out, g.nset[x]);
+  return out;
 }
 
-// Q(S, v) itself (same search, collecting the vertices instead of counting).
+// The vertices of `inside` that v reaches by a path whose vertices after v
+// all lie in `inside`, collected by path length: the ones at distance 1,
+// then those adjacent to a collected one, and so on until nothing is added.
+Key reach_within(const Graph& g, const Key& inside, int v) {
+  Key reached = set_meet(g.nset[v], inside);
+  Key newest = reached;
+  while (!is_empty(newest)) {
+    newest = set_minus(set_meet(neighbours_of(g, newest), inside), reached);
+    reached = set_union(reached, newest);
+  }
+  return reached;
+}
+
+// Q(S, v) of Section 2: a path from v to u with every inner vertex in S is
+// v - x_1 - ... - x_m - u with x_1 .. x_m in S (m = 0 allowed), so u is a
+// neighbour of v or of a vertex of S that v reaches through S.  Reading R1
+// leaves v out; vertices of S are never in Q.
 Key q_set(const Graph& g, const Key& S, int v) {
-  char visited[kMaxN];
-  int stack[kMaxN + 1];
-  std::memset(visited, 0, sizeof(visited));
-  Key q{{0, 0}};
-  int top = 0;
-  visited[v] = 1;
-  stack[top++] = v;
-  while (top > 0) {
-    const int u = stack[--top];
-    for (int w : g.nbr[u]) {
-      if (visited[w]) continue;
-      visited[w] = 1;
-      if (has(S, w))
-        stack[top++] = w;
-      else
-        q = with(q, w);
-    }
-  }
-  return q;
+  const Key inner = reach_within(g, S, v);
+  const Key ends = set_union(g.nset[v], neighbours_of(g, inner));
+  return without(set_minus(ends, S), v);
 }
 
-int popcount_key(const Key& s) { return __builtin_popcountll(s.w[0]) + __builtin_popcountll(s.w[1]); }
-
-int lowest_vertex(const Key& s) { return s.w[0] ? __builtin_ctzll(s.w[0]) : 64 + __builtin_ctzll(s.w[1]); }
+int q_size(const Graph& g, const Key& S, int v) { return popcount_key(q_set(g, S, v)); }
 
 // Whether v lies in the component of G[S u {v}] that contains the lowest
-// vertex of S u {v} (a depth-first search from v that stays inside S u {v}).
+// vertex of S u {v}.
 bool in_lowest_component(const Graph& g, const Key& S, int v) {
   const Key T = with(S, v);
   const int low = lowest_vertex(T);
-  char visited[kMaxN];
-  int stack[kMaxN + 1];
-  std::memset(visited, 0, sizeof(visited));
-  int top = 0;
-  visited[v] = 1;
-  stack[top++] = v;
-  while (top > 0) {
-    const int u = stack[--top];
-    for (int w : g.nbr[u]) {
-      if (visited[w] || !has(T, w)) continue;
-      visited[w] = 1;
-      stack[top++] = w;
-    }
-  }
-  return visited[low] != 0;
+  return low == v || has(reach_within(g, T, v), low);
 }
 
 struct DecideOut {
@@ -204,83 +193,99 @@ struct DecideOut {
 
 int mmw_bound(const Graph& g, const Key& S, int stop_above);
 
-// Listing 1 for one value of k, with exact sets (reading R4).  Only vertices
-// with allowed[v] are added to sets (all of them in the plain method).  With
-// mmw_prune, a set whose remaining graph has a minor-min-width bound above k
-// (Section 3.3) is not extended.
-// With max_level >= 0 the run stops after building level max_level (the
-// first levels of a run too large to finish here; yes is then not decided).
+// A level L_i: every set, mapped to one vertex v whose removal leaves a set
+// of L_{i-1} from which it was obtained (-1 for the empty set).
+using Level = std::unordered_map<Key, int, KeyHash>;
+
+// What a run of the test may change (everything off is the plain method).
+struct RunRule {
+  const std::vector<char>* allowed = nullptr;  // only these vertices may join a set
+  bool mmw_prune = false;                       // Section 3.3 bound on each set
+  bool count_canonical = false;
+};
+
+// L_{i+1} from L_i (Section 3.1): every S u {v} with v outside S and
+// |Q(S, v)| <= k, keeping for each new set the first v that produced it.
+// Adds the counters of this step to *out.
+Level grow_level(const Graph& g, int k, const Level& Li, const RunRule& rule, DecideOut* out) {
+  Level next;
+  for (const auto& entry : Li) {
+    const Key& S = entry.first;
+    std::vector<int> outside;
+    for (int v = 0; v < g.n; ++v)
+      if (!has(S, v) && (!rule.allowed || (*rule.allowed)[v])) outside.push_back(v);
+    out->candidates += (int64_t)outside.size();
+    if (rule.mmw_prune && mmw_bound(g, S, k) > k) continue;
+    for (int v : outside) {
+      if (q_size(g, S, v) > k) continue;
+      ++out->feasible;
+      if (rule.count_canonical && in_lowest_component(g, S, v)) ++out->canonical;
+      next.emplace(with(S, v), v);  // keeps the first producer
+    }
+  }
+  out->states_expanded += (int64_t)Li.size();
+  return next;
+}
+
+// The test at bound k with exact sets (reading R4).  With max_level >= 0 the
+// run stops after building level max_level (the first levels of a run too
+// large to finish here; yes is then not decided).  When keep is given it
+// receives every level built (level 0 first).
 void decide(const Graph& g, int k, bool want_order, DecideOut* out, const std::vector<char>* allowed = nullptr,
-            bool mmw_prune = false, bool count_canonical = false, int max_level = -1) {
+            bool mmw_prune = false, bool count_canonical = false, int max_level = -1,
+            std::vector<Level>* keep = nullptr) {
   const int n = g.n;
   out->level_size.assign(n + 1, 0);
   out->fp_sum.assign(n + 1, 0);
   out->fp_xor.assign(n + 1, 0);
   out->order.clear();
+  RunRule rule;
+  rule.allowed = allowed;
+  rule.mmw_prune = mmw_prune;
+  rule.count_canonical = count_canonical;
 
-  // Each level maps a set to one predecessor vertex (the v that first
-  // produced it); level 0 holds the empty set.
-  std::vector<std::unordered_map<Key, int, KeyHash>> kept;
-  std::unordered_map<Key, int, KeyHash> inp;
-  inp.emplace(Key{{0, 0}}, -1);
-  out->level_size[0] = 1;
-  out->fp_sum[0] = set_fingerprint(Key{{0, 0}});
-  out->fp_xor[0] = out->fp_sum[0];
-  int last = 0;
-
-  for (int i = 0; i <= n - k - 2 && (max_level < 0 || i < max_level); ++i) {
-    std::unordered_map<Key, int, KeyHash> outp;
-    for (const auto& entry : inp) {
-      const Key& S = entry.first;
-      int free_vertices = 0;
-      for (int v = 0; v < n; ++v)
-        if (!has(S, v) && (!allowed || (*allowed)[v])) ++free_vertices;
-      out->candidates += free_vertices;
-      if (mmw_prune && mmw_bound(g, S, k) > k) continue;
-      for (int v = 0; v < n; ++v) {
-        if (has(S, v)) continue;
-        if (allowed && !(*allowed)[v]) continue;
-        const int degree = dfs_degree(g, S, v);
-        if (degree <= k) {
-          ++out->feasible;
-          if (count_canonical && in_lowest_component(g, S, v)) ++out->canonical;
-          outp.emplace(with(S, v), v);  // keeps the first predecessor
-        }
-      }
-    }
-    out->states_expanded += (int64_t)inp.size();
-    if (want_order) kept.push_back(std::move(inp));
-    inp = std::move(outp);
-    last = i + 1;
-    out->level_size[last] = (int64_t)inp.size();
+  std::vector<Level> L(1);
+  L[0].emplace(kNoVertex, -1);
+  auto record = [&](int i) {
     uint64_t s = 0, x = 0;
-    for (const auto& entry : inp) {
-      const uint64_t f = set_fingerprint(entry.first);
+    for (const auto& e : L[i]) {
+      const uint64_t f = set_fingerprint(e.first);
       s += f;
       x ^= f;
     }
-    out->fp_sum[last] = s;
-    out->fp_xor[last] = x;
-    if (inp.empty()) break;  // reading R2
+    out->level_size[i] = (int64_t)L[i].size();
+    out->fp_sum[i] = s;
+    out->fp_xor[i] = x;
+  };
+  record(0);
+  const int top = n - k - 1;  // the level whose non-emptiness answers yes
+  const int stop = max_level >= 0 ? std::min(top, max_level) : top;
+  while ((int)L.size() - 1 < stop && !L.back().empty()) {
+    Level next = grow_level(g, k, L.back(), rule, out);
+    if (!want_order && !keep) L.back().clear();  // only the newest level is still needed
+    L.push_back(std::move(next));
+    record((int)L.size() - 1);
   }
+  const int last = (int)L.size() - 1;
   out->levels = last + 1;
-  out->yes = inp.empty() ? 0 : 1;
+  out->yes = L[last].empty() ? 0 : 1;
 
   if (want_order && out->yes) {
-    // Walk back from any final set through the recorded predecessors.
-    Key S = inp.begin()->first;
+    // From any set of the last level, drop the recorded producers one level
+    // at a time; they are the first vertices of the ordering, in reverse.
+    Key S = L[last].begin()->first;
     const Key final_set = S;
-    std::vector<int> prefix(last, -1);
+    std::vector<int> first(last, -1);
     for (int j = last; j >= 1; --j) {
-      const auto& level = (j == last) ? inp : kept[j];
-      const int v = level.at(S);
-      prefix[j - 1] = v;
+      const int v = L[j].at(S);
+      first[j - 1] = v;
       S = without(S, v);
     }
-    out->order = prefix;
+    out->order = first;
     for (int v = 0; v < n; ++v)
       if (!has(final_set, v)) out->order.push_back(v);
   }
+  if (keep) *keep = std::move(L);
 }
 
 // Width of an ordering through Q (Section 2's definition).
@@ -295,7 +300,7 @@ int width_by_q(const Graph& g, const int* order) {
   int width = 0;
   for (int j = 0; j < n; ++j) {
     const int v = order[j];
-    width = std::max(width, dfs_degree(g, prefix, v));
+    width = std::max(width, q_size(g, prefix, v));
     prefix = with(prefix, v);
   }
   return width;
@@ -337,11 +342,11 @@ int orc_valid_graph(const uint64_t* adj, int n) {
   return load_graph(adj, n, &g) ? 1 : 0;
 }
 
-// |Q(S, v)| through the Listing-1 search.  S is given as two words.
+// |Q(S, v)| (Section 2).  S is given as two words.
 int orc_q_size(const uint64_t* adj, int n, uint64_t s0, uint64_t s1, int v) {
   Graph g;
   if (!load_graph(adj, n, &g) || v < 0 || v >= n) return -1;
-  return dfs_degree(g, Key{{s0, s1}}, v);
+  return q_size(g, Key{{s0, s1}}, v);
 }
 
 // Q(S, v) as two words.
@@ -354,7 +359,7 @@ int orc_q_set(const uint64_t* adj, int n, uint64_t s0, uint64_t s1, int v, uint6
   return 0;
 }
 
-// One run of Listing 1 at bound k.  Arrays level_size / fp_sum / fp_xor have
+// One run of the Section 3.1 test (Listing 1) at bound k.  Arrays level_size / fp_sum / fp_xor have
 // n+1 entries (entries past the last level are zero).  counters[0..2] =
 // states expanded, candidates, feasible candidates.  order (n entries, or
 // NULL) receives an elimination ordering of width <= k when the answer is
@@ -381,7 +386,7 @@ int orc_decide(const uint64_t* adj, int n, int k, int64_t* level_size, uint64_t*
   return out.yes;
 }
 
-// Iterative deepening (Listing 1, outer loop) from k_start upward; the first
+// Iterative deepening (Section 3.1) from k_start upward; the first
 // yes is the treewidth.  counters[0..2] are summed over every k tried;
 // counters[3] = number of k tried.  Returns tw or -1.
 int orc_solve(const uint64_t* adj, int n, int k_start, int32_t* order, int64_t* counters) {
@@ -793,11 +798,7 @@ int orc_decide_opts(const uint64_t* adj, int n, int k, int opts, int64_t* level_
     for (int u = 0; u < n; ++u)
       for (int v = u + 1; v < n; ++v)
         if (!g0.mat[u][v] && disjoint_paths(g0, u, v, k + 1) >= k + 1) g.mat[u][v] = g.mat[v][u] = 1;
-    for (int u = 0; u < n; ++u) {
-      g.nbr[u].clear();
-      for (int v = 0; v < n; ++v)
-        if (g.mat[u][v]) g.nbr[u].push_back(v);
-    }
+    derive_lists(&g);
   }
   DecideOut out;
   std::vector<char> allowed(n, 1);

@@ -15,26 +15,26 @@ from tests.test_oracle_canonical import _levels
 SRC = os.path.join(os.path.dirname(oracle.__file__), "tw_oracle.cpp")
 
 MUTANTS = {
-    "v_not_marked_visited": ("  visited[v] = 1;\n  stack[top++] = v;\n  while (top > 0) {\n    const int u = stack[--top];\n"
-                             "    for (int w : g.nbr[u]) {\n      if (visited[w]) continue;\n      visited[w] = 1;\n"
-                             "      if (has(S, w))\n        stack[top++] = w;\n      else\n        ++degree;",
-                             "  stack[top++] = v;\n  while (top > 0) {\n    const int u = stack[--top];\n"
-                             "    for (int w : g.nbr[u]) {\n      if (visited[w]) continue;\n      visited[w] = 1;\n"
-                             "      if (has(S, w))\n        stack[top++] = w;\n      else\n        ++degree;"),
-    "strict_degree_bound": ("if (degree <= k) {", "if (degree < k) {"),
-    "one_level_short": ("for (int i = 0; i <= n - k - 2 && (max_level < 0 || i < max_level); ++i) {",
-                        "for (int i = 0; i <= n - k - 3 && (max_level < 0 || i < max_level); ++i) {"),
-    "branches_swapped": ("      if (has(S, w))\n        stack[top++] = w;\n      else\n        ++degree;",
-                         "      if (!has(S, w))\n        stack[top++] = w;\n      else\n        ++degree;"),
-    "wrong_vertex_added": ("outp.emplace(with(S, v), v);", "outp.emplace(with(S, (v + 1) % n), v);"),
+    "v_in_its_own_q": ("return without(set_minus(ends, S), v);", "return set_minus(ends, S);"),
+    "q_misses_direct_neighbours": ("const Key ends = set_union(g.nset[v], neighbours_of(g, inner));",
+                                   "const Key ends = neighbours_of(g, inner);"),
+    "reach_stops_after_one_step": ("  while (!is_empty(newest)) {\n    newest = set_minus(",
+                                   "  while (!is_empty(newest) && false) {\n    newest = set_minus("),
+    "reach_leaves_s": ("newest = set_minus(set_meet(neighbours_of(g, newest), inside), reached);",
+                       "newest = set_minus(set_minus(neighbours_of(g, newest), inside), reached);"),
+    "strict_degree_bound": ("if (q_size(g, S, v) > k) continue;", "if (q_size(g, S, v) >= k) continue;"),
+    "one_level_short": ("const int top = n - k - 1;", "const int top = n - k - 2;"),
+    "wrong_vertex_added": ("next.emplace(with(S, v), v);", "next.emplace(with(S, (v + 1) % g.n), v);"),
     "fill_in_self_loop": ("if ((nb >> u) & 1u) r |= nb & ~(1u << u);", "if ((nb >> u) & 1u) r |= nb;"),
     "width_off_by_one": ("width = std::max(width, (int)nb.size());", "width = std::max(width, (int)nb.size() - 1);"),
-    "no_stop_at_empty_level": ("    if (inp.empty()) break;  // reading R2\n", ""),
+    "no_stop_at_empty_level": ("while ((int)L.size() - 1 < stop && !L.back().empty()) {",
+                               "while ((int)L.size() - 1 < stop) {"),
     "fingerprint_constant": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 27)) * 0x94D049BB133111EDULL;"),
     "canonical_highest_vertex": ("const int low = lowest_vertex(T);",
                                  "const int low = T.w[1] ? 127 - __builtin_clzll(T.w[1]) : 63 - __builtin_clzll(T.w[0]);"),
-    "canonical_search_leaves_set": ("if (visited[w] || !has(T, w)) continue;", "if (visited[w]) continue;"),
-    "prefix_one_level_short": ("(max_level < 0 || i < max_level)", "(max_level < 0 || i < max_level - 1)"),
+    "canonical_search_leaves_set": ("return low == v || has(reach_within(g, T, v), low);",
+                                    "return low == v || has(reach_within(g, Key{{~0ULL, ~0ULL}}, v), low);"),
+    "prefix_one_level_short": ("std::min(top, max_level) : top;", "std::min(top, max_level - 1) : top;"),
 }
 
 
