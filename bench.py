@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--mem-cap-gb", type=float, default=0.0, help="device memory cap per context (0 = default)")
     ap.add_argument("--spill-levels", action="store_true",
                     help="keep finished levels in pinned host memory (tw_config.spill_levels)")
+    ap.add_argument("--no-sub", action="store_true", help="skip the other workloads' sub-records")
+    ap.add_argument("--ncu-record", nargs=2, metavar=("CSV", "FIRST_LEVEL"),
+                    help="write profiles/expand_insert_rgg40_counters.json from an ncu CSV of consecutive "
+                         "expand launches starting at FIRST_LEVEL, then exit")
+    ap.add_argument("--ncu-command", default="", help="the ncu command line recorded with --ncu-record")
     return ap.parse_args()
 
 
@@ -128,25 +133,38 @@ def job_throughput(units_per_rank: float, world: int, slowest_seconds: float) ->
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_sample(seconds: float):
-    """The CPU oracle as it stands on a bounded sample of the workload: the
-    decide runs k = 0..5 of the same graph's plain sweep (the runs before the
-    yes at tw = 6), repeated until `seconds` have passed."""
+# The timed GPU step is one tw_solve of the n=40 geometric graph: its lower
+# bound is already tw = 6, so the step is the single decide run at k = 6
+# (79,399,414 states).  The oracle cannot finish that run in a bounded sample,
+# so its sample is the start of the same run: decide(6) up to level 8, i.e.
+# the expansion of levels 0 .. 7 (304,654 states), repeated.
+ORACLE_K = 6
+ORACLE_LEVELS = 8
+
+
+def oracle_step():
+    """One bounded oracle sample: levels 0 .. ORACLE_LEVELS of decide(6) of the
+    benchmark graph; returns the states it expanded."""
     import oracle
     from paper_1709_09990_gb300 import graphgen as gg
-    adj = gg.workload_rgg40()
+    return oracle.decide_prefix(gg.workload_rgg40(), ORACLE_K, ORACLE_LEVELS, count_canonical=False)["states_expanded"]
+
+
+def oracle_sample(seconds: float):
+    """The CPU oracle as it stands, timed on the host for at least `seconds`
+    over repeats of :func:`oracle_step`."""
     states = 0
     runs = 0
     t0 = time.perf_counter()
     while True:
-        for k in range(0, 6):
-            states += oracle.decide(adj, k)["states_expanded"]
+        states += oracle_step()
         runs += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
     return {"value": states / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle decide(k) for k=0..5 on the same graph, {runs} pass(es), {states} states in {dt:.1f} s"}
+            "sample": f"the first {ORACLE_LEVELS} levels of the same decide run (k={ORACLE_K}; {states // runs} of its "
+                      f"79,399,414 states) on one host core, {runs} repeat(s), {states} states in {dt:.1f} s"}
 
 
 def peaks():
@@ -170,16 +188,151 @@ def kernel_source_hash() -> str:
     return hashlib.sha256("\n".join(code).encode()).hexdigest()
 
 
-def expand_traffic():
-    """Per-launch DRAM traffic of the expand kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
+COUNTERS = os.path.join(ROOT, "profiles", "expand_insert_rgg40_counters.json")
+
+
+def expand_counters():
+    """The committed ncu counters of a few expand launches of the benchmark
+    step (see write_counter_record), or None when the kernel source changed
+    since they were taken."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "expand_insert_rgg40_traffic.json")))
+        rec = json.load(open(COUNTERS))
     except (OSError, ValueError):
         return None
     if rec.get("source_sha256") != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
+
+
+def write_counter_record(csv_path: str, first_level: int, command: str) -> dict:
+    """Turns the ncu CSV of consecutive expand launches (levels first_level,
+    first_level + 1, ... of the benchmark's decide run) into the counter
+    record the bench reads: per launch DRAM bytes, ALU-pipe and total warp
+    instructions, duration, and the ALU pipe's peak rate."""
+    import csv
+    by_id, names = {}, set()
+    for row in csv.DictReader(l for l in open(csv_path) if l.startswith('"')):
+        if "expand" not in row.get("Kernel Name", ""):
+            continue
+        names.add(row["Kernel Name"])
+        v = row["Metric Value"].replace(",", "")
+        by_id.setdefault(int(row["ID"]), {})[row["Metric Name"]] = float(v)
+    launches = [by_id[i] for i in sorted(by_id)]
+    rec = {"kernel": " / ".join(sorted(names)),
+           "workload": "random geometric graph n=40 r=0.25 seed 0, decide(6) of one tw_solve",
+           "levels": [first_level + j for j in range(len(launches))],
+           "dram_bytes": [m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"] for m in launches],
+           "alu_warp_inst": [m["sm__inst_executed_pipe_alu.sum"] for m in launches],
+           "warp_inst": [m["smsp__inst_executed.sum"] for m in launches],
+           "duration_ns": [m["gpu__time_duration.sum"] for m in launches],
+           "alu_pct_of_peak": [m["sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active"] for m in launches],
+           "alu_peak_warp_inst_per_sm_cycle": launches[0]["sm__inst_executed_pipe_alu.avg.peak_sustained"],
+           "source_sha256": kernel_source_hash(), "command": command,
+           "scaling": "per input state: the step's launches are credited with the captured launches' "
+                      "counts per input state times their own input states"}
+    with open(COUNTERS, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
+
+
+def roofline_of(st, pk, clocks):
+    """The expand kernel's rooflines for one step's statistics: ALU pipe (the
+    bound its profile shows on this L2-resident workload) and HBM."""
+    if not st["expand_seconds"]:
+        return None
+    launches = max(1, st["expand_launches"])
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
+    hbm_achieved = st["expand_bytes"] / st["expand_seconds"] / 1e9
+    out = {"kernel": "the expand+insert kernel (core::expand_level; graph_expand_kernel<uint64, 4 warps> in the "
+                     "graph-driven level loop the step runs)",
+           "launch_ms": 1e3 * st["expand_seconds"] / launches,
+           "bytes_per_launch": st["expand_bytes"] / launches,
+           "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                   "frac": round(hbm_achieved / hbm_peak, 4), "peak_source": "measured" if pk else "fallback"}}
+    rec = expand_counters()
+    traffic = None
+    if rec:
+        sizes = st["level_size"]
+        cap_states = sum(sizes[i] for i in rec["levels"])
+        per_state = lambda xs: sum(xs) / cap_states  # noqa: E731
+        traffic = per_state(rec["dram_bytes"]) * st["states_expanded"] / launches
+        alu_inst = per_state(rec["alu_warp_inst"]) * st["states_expanded"]
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        sms = 152
+        alu_peak = rec["alu_peak_warp_inst_per_sm_cycle"] * sms * sm_mhz * 1e6 / 1e9
+        alu_achieved = alu_inst / st["expand_seconds"] / 1e9
+        out.update({"bound": "alu", "achieved": round(alu_achieved, 1), "peak": round(alu_peak, 1),
+                    "unit": "G ALU-pipe warp-instructions/s", "frac": round(alu_achieved / alu_peak, 4),
+                    "traffic": round(traffic, 1),
+                    "alu_frac": round(alu_achieved / alu_peak, 4),
+                    "alu_frac_ncu_captured": [round(x / 100.0, 4) for x in rec["alu_pct_of_peak"]],
+                    "peak_note": f"{rec['alu_peak_warp_inst_per_sm_cycle']} ALU warp-instructions per SM cycle "
+                                 f"(ncu peak_sustained) x {sms} SMs x {sm_mhz:.0f} MHz (median SM clock under load)",
+                    "counters_from": f"ncu, levels {rec['levels']} of the step, scaled per input state"})
+    else:
+        out.update({"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(hbm_achieved / hbm_peak, 4), "traffic": None})
+    out["hbm"]["traffic_over_algorithmic"] = round(traffic / out["bytes_per_launch"], 3) if traffic else None
+    return out
+
+
+# ------------------------------------------------------ other workloads
+def sub_gnp20(stream, steps):
+    """G(20, 0.3) seed 0 (32-bit states): the plain sweep from the lower bound
+    with ordering and tree decomposition; CUDA events on libtw's stream."""
+    import numpy as np
+    import torch
+    from paper_1709_09990_gb300 import graphgen as gg
+    from paper_1709_09990_gb300 import native
+    adj = gg.workload_gnp20()
+    rows = torch.from_numpy(gg.to_rows_u64(adj).astype(np.int64)).cuda()
+    with native.Context(device=torch.cuda.current_device(), stream=stream.cuda_stream) as ctx:
+        for _ in range(3):
+            res = ctx.solve(rows, n=20, want_td=True)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches = 0
+        for a, b in ev:
+            a.record(stream)
+            res = ctx.solve(rows, n=20, want_td=True)
+            b.record(stream)
+            launches += res["stats"]["kernel_launches"]
+        torch.cuda.synchronize()
+    dt = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    st = res["stats"]
+    return {"workload": "G(n=20, p=0.3) seed 0; plain sweep from the lower bound to exact tw, ordering + tree "
+                        "decomposition", "dtype": "u32", "tw": res["tw"], "metric": METRIC,
+            "value": round(st["states_expanded"] * steps / dt, 1), "unit": UNIT,
+            "time_to_exact_tw_ms": round(1e3 * dt / steps, 4), "states_per_solve": st["states_expanded"],
+            "decide_runs": st["decide_runs"], "gpu_launches_per_solve": launches // steps,
+            "level_sizes_final_k": st["level_size"], "steps": steps}
+
+
+def sub_pktree60(args):
+    """The partial 10-tree n=60 seed 0 at k = 10 under the default cap
+    (150 GB or 90% of free memory): the levels reached, with the Section 3.1
+    clique skip on (it shrinks this graph's wavefront) and off."""
+    from paper_1709_09990_gb300 import graphgen as gg
+    from paper_1709_09990_gb300 import native
+    adj = gg.workload_pktree60()
+    out = {"workload": "partial 10-tree n=60 (30% of edges removed) seed 0; decide at k=10", "dtype": "u64"}
+    for name, kw in (("plain", {}), ("clique_skip", {"clique_skip": True})):
+        with native.Context(device=0, time_kernels=True, **kw) as ctx:
+            b = ctx.bounds(adj).tolist()
+            t = time.perf_counter()
+            r = ctx.decide(adj, k=10, raise_on_error=False)
+            dt = time.perf_counter() - t
+        st = r["stats"]
+        out[name] = {"status": native.strerror(r["status"]), "yes": r["yes"] if r["status"] == 0 else None,
+                     "seconds": round(dt, 3), "levels_reached": st["level_size"],
+                     "states_expanded": st["states_expanded"], "states_per_s": round(st["states_expanded"] / dt, 1),
+                     "peak_frontier_bytes": st["peak_frontier_bytes"],
+                     "expand_algorithmic_GBps": round(st["expand_bytes"] / st["expand_seconds"] / 1e9, 1)
+                     if st["expand_seconds"] else None}
+        out["bounds"] = {"mmd": b[0], "mmd_plus": b[1], "min_degree_width": b[2], "min_fill_width": b[3]}
+        out["tw_from_bounds"] = b[1] if max(b[0], b[1]) == min(b[2], b[3]) else None
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -238,11 +391,14 @@ def run_ours(args):
     states_step = stats[-1]["states_expanded"]
     value = job_throughput(states_step * args.steps, world, dev_s)
 
-    # end to end through the C ABI with host buffers (pinned)
+    # end to end through the C ABI with host buffers (pinned), the same
+    # outputs as the device step: tw, ordering, tree decomposition
+    words = max(1, (n + 63) // 64)
     rows_pin = torch.from_numpy(rows_host).pin_memory()
     tw_pin = torch.full((1,), -1, dtype=torch.int32).pin_memory()
     order_pin = torch.full((n,), -1, dtype=torch.int32).pin_memory()
     parent_pin = torch.full((n,), -1, dtype=torch.int32).pin_memory()
+    bags_pin = torch.zeros((n, words), dtype=torch.int64).pin_memory()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -253,24 +409,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         native.lib().tw_solve(ctx._h, rows_pin.data_ptr(), n, tw_pin.data_ptr(), order_pin.data_ptr(),
-                              parent_pin.data_ptr(), None, None)
+                              parent_pin.data_ptr(), bags_pin.data_ptr(), None)
         e2e_s += time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dev)
     assert int(tw_pin[0]) == tw
 
     st = stats[-1]
-    pk = peaks()
-    achieved = st["expand_bytes"] / st["expand_seconds"] / 1e9 if st["expand_seconds"] > 0 else None
-    traffic = expand_traffic()
-    roofline = None
-    if achieved is not None:
-        peak = pk["hbm_gbs"] if pk else 6800.0
-        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": traffic,
-                    "kernel": "expand_insert_kernel<uint64, 4 warps, 4 in flight>",
-                    "peak_source": "measured" if pk else "fallback",
-                    "bytes_per_launch": st["expand_bytes"] / max(1, st["expand_launches"]),
-                    "launch_ms": 1e3 * st["expand_seconds"] / max(1, st["expand_launches"])}
+    roofline = roofline_of(st, peaks(), clocks)
+    d2h = tw_pin.nbytes + order_pin.nbytes + parent_pin.nbytes + bags_pin.nbytes
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(1e3 * dev_s / args.steps, 3), "higher_is_better": True,
@@ -281,10 +427,15 @@ def run_ours(args):
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "time_to_exact_tw_ms": round(1e3 * dev_s / args.steps, 3),
            "e2e": {"value": round(job_throughput(states_step * args.steps, world, e2e_s), 1), "unit": UNIT,
-                   "h2d_bytes_per_step": int(rows_host.nbytes), "d2h_bytes_per_step": 4 + 8 * n,
-                   "ms_per_step": round(1e3 * e2e_s / args.steps, 3)},
+                   "h2d_bytes_per_step": int(rows_host.nbytes), "d2h_bytes_per_step": int(d2h),
+                   "ms_per_step": round(1e3 * e2e_s / args.steps, 3),
+                   "outputs": "tw, ordering, tree decomposition (parents and bags), as in the device-timed step"},
            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
            "roofline": roofline, "clocks": clocks}
+    if world == 1 and not args.no_sub:
+        # the other single-graph workloads, after the timed region
+        out["other_workloads"] = {"gnp20": sub_gnp20(stream, max(5, args.steps)),
+                                  "pktree60": sub_pktree60(args)}
     ctx.close()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
@@ -297,7 +448,7 @@ def run_ours(args):
 # ----------------------------------------------------------- reference arm
 def run_reference(args):
     """The CPU oracle on rank 0: each step is the bounded oracle sample of the
-    same workload (decide k = 0..5)."""
+    same workload (the first levels of the same decide run)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -305,12 +456,7 @@ def run_reference(args):
     from paper_1709_09990_gb300 import graphgen as gg
     adj = gg.workload_rgg40()
     oracle.build()
-
-    def step():
-        s = 0
-        for k in range(0, 6):
-            s += oracle.decide(adj, k)["states_expanded"]
-        return s
+    step = oracle_step
 
     for _ in range(args.warmup):
         step()
@@ -320,7 +466,8 @@ def run_reference(args):
         states += step()
     dt = time.perf_counter() - t0
     value = states / dt
-    sample = f"oracle decide(k) for k=0..5 of the workload graph per step ({states // max(1, args.steps)} states)"
+    sample = (f"oracle: the first {ORACLE_LEVELS} levels of the benchmark step's decide run (k={ORACLE_K}; "
+              f"{states // max(1, args.steps)} of its 79,399,414 states) per step, one host core")
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -497,6 +644,9 @@ def run_learned(args):
 
 def main():
     args = parse()
+    if args.ncu_record:
+        print(json.dumps(write_counter_record(args.ncu_record[0], int(args.ncu_record[1]), args.ncu_command)))
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "rgg40":

@@ -42,7 +42,7 @@ extern "C" {
 #endif
 
 #define TW_MAX_N 128
-#define TW_ABI_VERSION 2
+#define TW_ABI_VERSION 3
 
 /* Status codes. */
 #define TW_OK 0
@@ -172,6 +172,23 @@ void tw_destroy(tw_ctx* ctx);
 int tw_decide(tw_ctx* ctx, const uint64_t* adj, int n, int k, int* yes, int32_t* order,
               tw_stats* st);
 
+/* The wavefront itself: the sets of level `level` of decide(k) (Section 3.1,
+ * Listing 1; the same run as tw_decide with the context's options, stopped
+ * once that level is built).
+ *   level : 0 .. n; a level after the run's last one (the run ended at an
+ *           empty level, or level > n-k-1) has no sets.
+ *   keys  : out, cap sets of W = ceil(n/64) uint64 words each (bit v of word
+ *           v/64 = vertex v), in no particular order.  May be NULL when cap
+ *           is 0.
+ *   cap   : room in keys, in sets.
+ *   count : out (required), |L_level|, also when it exceeds cap.
+ *   st    : out statistics of the run (or NULL).
+ * Returns TW_OK, or TW_ERR_CAPACITY when |L_level| > cap (nothing is written
+ * to keys; *count tells the caller how much room to pass), or the errors of
+ * tw_decide. */
+int tw_decide_level(tw_ctx* ctx, const uint64_t* adj, int n, int k, int level, uint64_t* keys, uint64_t cap,
+                    uint64_t* count, tw_stats* st);
+
 /* As tw_decide for n <= 32 with one uint32 word per row (bit c of row r =
  * edge rc).  Runs the 32-bit state kernel. */
 int tw_decide_u32(tw_ctx* ctx, const uint32_t* adj_rows, int n, int k, int* yes,
@@ -209,6 +226,26 @@ int tw_solve(tw_ctx* ctx, const uint64_t* adj, int n, int* tw, int32_t* order,
 int tw_solve_batch(tw_ctx* ctx, const uint64_t* adj_concat, const int32_t* n,
                    const int64_t* row_offset, int num_graphs, int* tw, int32_t* orders,
                    int* status, const float* k_hint, tw_stats* st);
+
+/* decide(k[g]) for many graphs of uneven size (Section 3.1, Listing 1 per
+ * graph), through the same batched kernel as tw_solve_batch (graphs with
+ * n > 64, and graphs whose levels outgrow the batch, run one at a time).
+ * The level sets are those of the plain method: clique_skip, disjoint_paths
+ * and mmw_prune are not applied.
+ *   adj_concat, n, row_offset : as tw_solve_batch.
+ *   k          : num_graphs bounds, k[g] >= 0.
+ *   yes        : out, num_graphs answers (1 iff tw(G_g) <= k[g]).
+ *   status     : out, num_graphs per-graph status.
+ *   level_size : out (or NULL), num_graphs rows of TW_MAX_N+1 uint64: row g
+ *                holds |L_0|, |L_1|, ... of graph g's run (up to and
+ *                including its first empty level), then zeros.
+ *   level_fp_sum, level_fp_xor : out (or NULL), the same layout: the sum and
+ *                xor of fp(S) over each level (see tw_stats).
+ *   st         : out (or NULL): totals over all graphs.
+ * Returns the worst per-graph status. */
+int tw_decide_batch(tw_ctx* ctx, const uint64_t* adj_concat, const int32_t* n, const int64_t* row_offset,
+                    int num_graphs, const int32_t* k, int* yes, int* status, uint64_t* level_size,
+                    uint64_t* level_fp_sum, uint64_t* level_fp_xor, tw_stats* st);
 
 /* Lower and upper bounds on the device (one warp per graph):
  * out[0] = minimum-degree (degeneracy) bound, out[1] = minor-min-width
@@ -266,14 +303,23 @@ int tw_mlp_train(tw_ctx* ctx, float* params, const float* x, const float* y, int
  *   d_out_pred : device, out_cap bytes: the vertex added to each output key.
  *   out_cap    : at most TW_STATIC_MAX_STATES; larger values return
  *                TW_ERR_INVALID without running.
- *   out_count  : host, receives |L_{i+1}| (also when it exceeds out_cap).
+ *   out_count  : host, receives |L_{i+1}|, also when it exceeds out_cap,
+ *                as long as the level fits the fixed table (about 2^21
+ *                states).  A level that fills the whole table yields
+ *                TW_ERR_CAPACITY with *out_count set above
+ *                TW_STATIC_MAX_STATES; the value is then only a lower bound,
+ *                and no call of this entry point can build that level.
  * Returns TW_OK; TW_ERR_CAPACITY when level i+1 has more than out_cap states
  * (or the fixed table overflows) - the output is then incomplete;
- * TW_ERR_INVALID for host pointers, n > 64 or out_cap too large;
- * TW_ERR_CUDA.  The first call on a device resolves the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call reuses the same array: calls that overlap on the GPU
- * (other streams, other host threads) race and corrupt each other. */
+ * TW_ERR_INVALID for host pointers, n > 64, out_cap too large, or, when
+ * n = 64, an input set of 63 or 64 vertices (its extension would be the
+ * all-ones set, which the table uses as its empty marker); TW_ERR_CUDA.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress).  Every call reads its counters back and
+ * synchronises the stream, so it must not be called while the stream is
+ * being captured into a CUDA graph.  Every call reuses the same array: calls
+ * that overlap on the GPU (other streams, other host threads) race and
+ * corrupt each other. */
 #define TW_STATIC_MAX_STATES (1ull << 20)
 int tw_expand_level_static(const uint64_t* d_in_keys, uint64_t n_in, const uint64_t* d_adj, int n, int k,
                            uint64_t* d_out_keys, uint8_t* d_out_pred, uint64_t out_cap,

@@ -73,7 +73,10 @@ def _bind(lib):
                                     _i64p, _i32p]
     if hasattr(lib, "orc_decide_prefix"):
         lib.orc_decide_prefix.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _u64p, _u64p,
-                                          _i64p]
+                                          _i64p, ctypes.c_int]
+    if hasattr(lib, "orc_level_keys"):
+        lib.orc_level_keys.restype = ctypes.c_int64
+        lib.orc_level_keys.argtypes = [_u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_int64]
     return lib
 
 
@@ -154,10 +157,11 @@ def decide(adj: Sequence[int], k: int, want_order: bool = False, count_canonical
             "order": order.tolist() if (order is not None and yes) else None}
 
 
-def decide_prefix(adj: Sequence[int], k: int, max_level: int) -> Dict:
-    """The first levels 0 .. max_level of Listing 1 at bound k (for runs too
-    large to finish here): level_size, fp_sum, fp_xor and the counters of the
-    levels expanded so far, canonical pairs included."""
+def decide_prefix(adj: Sequence[int], k: int, max_level: int, count_canonical: bool = True) -> Dict:
+    """The first levels 0 .. max_level of the Section 3.1 test at bound k (for
+    runs too large to finish here): level_size, fp_sum, fp_xor and the
+    counters of the levels expanded so far (canonical pairs included when
+    count_canonical)."""
     n = len(adj)
     r = rows(adj)
     ls = np.zeros(n + 1, dtype=np.int64)
@@ -165,12 +169,42 @@ def decide_prefix(adj: Sequence[int], k: int, max_level: int) -> Dict:
     fx = np.zeros(n + 1, dtype=np.uint64)
     cnt = np.zeros(4, dtype=np.int64)
     lv = _load().orc_decide_prefix(_ptr(r, _u64p), n, k, max_level, _ptr(ls, _i64p), _ptr(fs, _u64p),
-                                   _ptr(fx, _u64p), _ptr(cnt, _i64p))
+                                   _ptr(fx, _u64p), _ptr(cnt, _i64p), int(count_canonical))
     if lv < 0:
         raise ValueError("invalid graph, k or max_level")
-    return {"levels": lv, "level_size": ls[:lv].tolist(), "fp_sum": fs[:lv].tolist(), "fp_xor": fx[:lv].tolist(),
-            "states_expanded": int(cnt[0]), "candidates": int(cnt[1]), "feasible": int(cnt[2]),
-            "canonical": int(cnt[3])}
+    out = {"levels": lv, "level_size": ls[:lv].tolist(), "fp_sum": fs[:lv].tolist(), "fp_xor": fx[:lv].tolist(),
+           "states_expanded": int(cnt[0]), "candidates": int(cnt[1]), "feasible": int(cnt[2])}
+    if count_canonical:
+        out["canonical"] = int(cnt[3])
+    return out
+
+
+def level_keys(adj: Sequence[int], k: int, level: int) -> np.ndarray:
+    """The sets of level ``level`` of the test at bound k, as a
+    (|L_level|, ceil(n/64)) uint64 array sorted by rows (word 0 first)."""
+    n = len(adj)
+    r = rows(adj)
+    w = r.shape[1]
+    lib = _load()
+    count = lib.orc_level_keys(_ptr(r, _u64p), n, k, level, None, 0)
+    if count < 0:
+        raise ValueError("invalid graph, k or level")
+    out = np.zeros((max(1, count), w), dtype=np.uint64)
+    got = lib.orc_level_keys(_ptr(r, _u64p), n, k, level, _ptr(out, _u64p), count)
+    assert got == count
+    return sort_keys(out[:count])
+
+
+def sort_keys(keys: np.ndarray) -> np.ndarray:
+    """Rows of a (count, W) uint64 key array in increasing order (last word
+    most significant)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    if keys.ndim == 1:
+        keys = keys.reshape(len(keys), 1)
+    if len(keys) == 0:
+        return keys
+    idx = np.lexsort(tuple(keys[:, j] for j in range(keys.shape[1])))
+    return keys[idx]
 
 
 CLIQUE_SKIP, DISJOINT_PATHS, MMW_PRUNE, COUNT_CANONICAL = 1, 2, 4, 8

@@ -761,15 +761,15 @@ int orc_disjoint_paths(const uint64_t* adj, int n, int u, int v, int limit) {
   return disjoint_paths(g, u, v, limit);
 }
 
-// The first levels 0 .. max_level of orc_decide (canonical pairs counted
-// into counters[3]); for runs too large to finish.  Returns the number of
-// levels built, or -1 for invalid input.
+// The first levels 0 .. max_level of orc_decide (with count_canonical, the
+// canonical pairs are counted into counters[3]); for runs too large to
+// finish.  Returns the number of levels built, or -1 for invalid input.
 int orc_decide_prefix(const uint64_t* adj, int n, int k, int max_level, int64_t* level_size, uint64_t* fp_sum,
-                      uint64_t* fp_xor, int64_t* counters) {
+                      uint64_t* fp_xor, int64_t* counters, int count_canonical) {
   Graph g;
   if (!load_graph(adj, n, &g) || k < 0 || max_level < 0) return -1;
   DecideOut out;
-  decide(g, k, false, &out, nullptr, false, true, max_level);
+  decide(g, k, false, &out, nullptr, false, count_canonical != 0, max_level);
   for (int i = 0; i <= n; ++i) {
     if (level_size) level_size[i] = out.level_size[i];
     if (fp_sum) fp_sum[i] = out.fp_sum[i];
@@ -782,6 +782,27 @@ int orc_decide_prefix(const uint64_t* adj, int n, int k, int max_level, int64_t*
     counters[3] = out.canonical;
   }
   return out.levels;
+}
+
+// The sets of level `level` of the run at bound k (the run stops after that
+// level; a level past the end of the run is empty).  Writes up to cap sets,
+// each as W = ceil(n/64) words, in no particular order, and returns the
+// level's size, or -1 for invalid input.
+int64_t orc_level_keys(const uint64_t* adj, int n, int k, int level, uint64_t* keys, int64_t cap) {
+  Graph g;
+  if (!load_graph(adj, n, &g) || k < 0 || level < 0) return -1;
+  DecideOut out;
+  std::vector<Level> L;
+  decide(g, k, false, &out, nullptr, false, false, level, &L);
+  if (level >= (int)L.size()) return 0;
+  const int W = words_for(n);
+  int64_t j = 0;
+  for (const auto& e : L[level]) {
+    if (j < cap)
+      for (int w = 0; w < W; ++w) keys[j * W + w] = e.first.w[w];
+    ++j;
+  }
+  return j;
 }
 
 // orc_decide with the options of Sections 3.1 and 3.3: bit 0 of opts =

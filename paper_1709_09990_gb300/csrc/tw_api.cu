@@ -152,6 +152,16 @@ int tw_decide(tw_ctx* c, const uint64_t* adj, int n, int k, int* yes, int32_t* o
   return decide_graph(c, g, k, yes, order, st);
 }
 
+int tw_decide_level(tw_ctx* c, const uint64_t* adj, int n, int k, int level, uint64_t* keys, uint64_t cap,
+                    uint64_t* count, tw_stats* st) {
+  if (!c || !count || k < 0 || level < 0) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  HostGraph g;
+  int rc = load_graph(adj, n, &g);
+  if (rc) return rc;
+  return level_keys_graph(c, g, k, level, keys, cap, count, st);
+}
+
 int tw_decide_u32(tw_ctx* c, const uint32_t* adj_rows, int n, int k, int* yes, int32_t* order, tw_stats* st) {
   if (!c || !yes || !adj_rows || k < 0 || n < 1 || n > 32) return TW_ERR_INVALID;
   TW_CK(cudaSetDevice(c->device));
@@ -349,6 +359,54 @@ int tw_solve_batch(tw_ctx* c, const uint64_t* adj_concat, const int32_t* n, cons
   if ((rc = put(c, tw, htw.data(), (size_t)G * sizeof(int)))) return rc;
   if ((rc = put(c, status, hst.data(), (size_t)G * sizeof(int)))) return rc;
   if (orders && (rc = put(c, orders, hord.data(), hord.size() * 4))) return rc;
+  if (st) {
+    st->seconds = t.seconds();
+    st->kernel_launches = c->launches - launches0;
+  }
+  return worst;
+}
+
+int tw_decide_batch(tw_ctx* c, const uint64_t* adj_concat, const int32_t* n, const int64_t* row_offset,
+                    int num_graphs, const int32_t* k, int* yes, int* status, uint64_t* level_size,
+                    uint64_t* level_fp_sum, uint64_t* level_fp_xor, tw_stats* st) {
+  if (!c || !k || !yes || !status || num_graphs < 0) return TW_ERR_INVALID;
+  Timer t;
+  TW_CK(cudaSetDevice(c->device));
+  std::vector<int32_t> hn;
+  std::vector<int64_t> hoff;
+  std::vector<uint64_t> hadj;
+  int rc = load_batch(adj_concat, n, row_offset, num_graphs, &hn, &hoff, &hadj);
+  if (rc) return rc;
+  const int G = num_graphs;
+  std::vector<int32_t> hk(G);
+  if ((rc = fetch(hk.data(), k, (size_t)G * 4))) return rc;
+  std::vector<HostGraph> graphs(G);
+  std::vector<int> hst(G, TW_OK), valid, hyes(G, 0), kk(G, 0);
+  for (int g = 0; g < G; ++g) {
+    hst[g] = validate(hadj.data() + hoff[g], hn[g], &graphs[g]);
+    if (hst[g] == TW_OK && hk[g] < 0) hst[g] = TW_ERR_INVALID;
+    if (hst[g] == TW_OK) valid.push_back(g);
+    kk[g] = hk[g];
+  }
+  std::vector<std::vector<unsigned long long>> sizes(G), fs(G), fx(G);
+  if (st) std::memset(st, 0, sizeof(*st));
+  const unsigned long long launches0 = c->launches;
+  rc = decide_batch_gpu(c, graphs, valid, kk, &hyes, &hst, &sizes, level_fp_sum ? &fs : nullptr,
+                        level_fp_xor ? &fx : nullptr, st);
+  if (rc) return rc;
+  int worst = TW_OK;
+  for (int g = 0; g < G; ++g) worst = std::max(worst, hst[g]);
+  if ((rc = put(c, yes, hyes.data(), (size_t)G * sizeof(int)))) return rc;
+  if ((rc = put(c, status, hst.data(), (size_t)G * sizeof(int)))) return rc;
+  const size_t L = TW_MAX_N + 1;
+  auto flat = [&](const std::vector<std::vector<unsigned long long>>& v, uint64_t* dst) -> int {
+    if (!dst) return TW_OK;
+    std::vector<uint64_t> h((size_t)G * L, 0ull);
+    for (int g = 0; g < G; ++g)
+      for (size_t i = 0; i < v[g].size() && i < L; ++i) h[(size_t)g * L + i] = v[g][i];
+    return put(c, dst, h.data(), h.size() * 8);
+  };
+  if ((rc = flat(sizes, level_size)) || (rc = flat(fs, level_fp_sum)) || (rc = flat(fx, level_fp_xor))) return rc;
   if (st) {
     st->seconds = t.seconds();
     st->kernel_launches = c->launches - launches0;

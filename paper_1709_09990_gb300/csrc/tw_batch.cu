@@ -100,6 +100,30 @@ __global__ void copy_segments_kernel(const CopySeg* __restrict__ segs, int nseg,
   }
 }
 
+// One block per segment (grid-stride): the sum and xor of the level
+// fingerprints of the segment's keys.
+__global__ void fingerprint_segments_kernel(const CopySeg* __restrict__ segs, int nseg,
+                                            const unsigned long long* __restrict__ keys, unsigned long long* out) {
+  for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
+    const CopySeg cs = segs[s];
+    unsigned long long sum = 0, x = 0;
+    for (unsigned long long i = threadIdx.x; i < cs.count; i += blockDim.x) {
+      const unsigned long long f = kfingerprint(keys[cs.src_off + i]);
+      sum += f;
+      x ^= f;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      sum += __shfl_xor_sync(kFull, sum, d);
+      x ^= __shfl_xor_sync(kFull, x, d);
+    }
+    if ((threadIdx.x & 31) == 0 && (sum | x)) {
+      atomicAdd(&out[2 * s], sum);
+      atomicXor(&out[2 * s + 1], x);
+    }
+  }
+}
+
 // One thread per finished graph: walk the parent indices from the first state
 // of the last level down to level 0, then append the vertices outside the
 // final set in increasing order.
@@ -161,6 +185,14 @@ cudaError_t launch_copy_segments(const CopySeg* segs, int nseg, const unsigned l
   if (nseg == 0) return cudaSuccess;
   const int grid = nseg < sms() * 8 ? nseg : sms() * 8;
   copy_segments_kernel<<<grid, 256, 0, s>>>(segs, nseg, src_keys, src_par, dst_keys, dst_par);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fingerprint_segments(const CopySeg* segs, int nseg, const unsigned long long* keys,
+                                        unsigned long long* out, cudaStream_t s) {
+  if (nseg == 0) return cudaSuccess;
+  const int grid = nseg < sms() * 8 ? nseg : sms() * 8;
+  fingerprint_segments_kernel<<<grid, 256, 0, s>>>(segs, nseg, keys, out);
   return cudaGetLastError();
 }
 

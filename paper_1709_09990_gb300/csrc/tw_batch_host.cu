@@ -41,6 +41,16 @@ struct BGraph {
   int64_t order_off = 0;
 };
 
+// Decide-only mode of run_batch (tw_decide_batch): every graph runs one
+// decide at its own k and reports its answer, level sizes and fingerprints.
+struct BatchDecide {
+  const std::vector<int>* k = nullptr;                             // by graph index
+  std::vector<int>* yes = nullptr;                                 // by graph index
+  std::vector<std::vector<unsigned long long>>* size = nullptr;    // by graph index
+  std::vector<std::vector<unsigned long long>>* fp_sum = nullptr;  // (or nullptr)
+  std::vector<std::vector<unsigned long long>>* fp_xor = nullptr;
+};
+
 template <class T>
 int dev_alloc(T** p, size_t count) {
   void* v = nullptr;
@@ -173,7 +183,8 @@ bool record_answer(BGraph& x, bool yes) {
 // returned in *evicted for the single-graph path.
 int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
               const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
-              std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st, std::vector<int>* evicted) {
+              std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st, std::vector<int>* evicted,
+              const BatchDecide* dm) {
   BatchRun B(c);
   const int G = (int)idx.size();
   if (G == 0) return TW_OK;
@@ -213,6 +224,7 @@ int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector
       int k0 = x.lb;
       if (hint) k0 = (int)std::lround((*hint)[idx[j]]);
       x.k0 = std::min(std::max(k0, x.lb), x.n - 1);
+      if (dm) x.k0 = (*dm->k)[idx[j]];  // 0 <= k < n-1 (the caller answers larger k)
       x.order_off = order_off[idx[j]];
     }
   }
@@ -259,18 +271,67 @@ int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector
     lvl.clear();
     std::vector<int> walked;
     bool answered = false;
-    for (int j = 0; j < G; ++j) {
-      BGraph& x = B.g[j];
-      if (x.state != 0) continue;
-      const int last = (int)x.levels.size() - 1;
-      if (x.levels.back().count == 0) {
-        record_answer(x, false);
-        x.levels.clear();
+    if (dm) {
+      // decide-only: record the run's levels (sizes and fingerprints) and stop
+      std::vector<int> fin;
+      std::vector<CopySeg> fseg;
+      for (int j = 0; j < G; ++j) {
+        BGraph& x = B.g[j];
+        if (x.state != 0) continue;
+        const int last = (int)x.levels.size() - 1;
+        if (x.levels.back().count != 0 && last != x.n - x.k - 1) continue;
+        fin.push_back(j);
+        for (const LevelRec& l : x.levels) fseg.push_back({l.off, 0ull, l.count});
+      }
+      if (!fin.empty()) {
+        std::vector<unsigned long long> fp(2 * fseg.size(), 0ull);
+        if (dm->fp_sum) {
+          CopySeg* d_seg = nullptr;
+          unsigned long long* d_fp = nullptr;
+          if ((rc = dev_alloc(&d_seg, fseg.size())) || (rc = dev_alloc(&d_fp, fp.size()))) return rc;
+          TW_CK(cudaMemcpyAsync(d_seg, fseg.data(), fseg.size() * sizeof(CopySeg), cudaMemcpyHostToDevice,
+                                c->stream));
+          TW_CK(cudaMemsetAsync(d_fp, 0, fp.size() * 8, c->stream));
+          TW_LAUNCH(c, launch_fingerprint_segments(d_seg, (int)fseg.size(), B.akeys, d_fp, c->stream));
+          TW_CK(cudaMemcpyAsync(fp.data(), d_fp, fp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+          TW_CK(cudaStreamSynchronize(c->stream));
+          cudaFree(d_seg);
+          cudaFree(d_fp);
+        }
+        size_t q = 0;
+        for (int j : fin) {
+          BGraph& x = B.g[j];
+          const int gi = x.in_idx;
+          (*dm->yes)[gi] = x.levels.back().count != 0 ? 1 : 0;
+          (*dm->size)[gi].clear();
+          if (dm->fp_sum) (*dm->fp_sum)[gi].clear();
+          if (dm->fp_xor) (*dm->fp_xor)[gi].clear();
+          for (const LevelRec& l : x.levels) {
+            (*dm->size)[gi].push_back(l.count);
+            if (dm->fp_sum) (*dm->fp_sum)[gi].push_back(fp[2 * q]);
+            if (dm->fp_xor) (*dm->fp_xor)[gi].push_back(fp[2 * q + 1]);
+            ++q;
+          }
+          x.tw = x.k;
+          x.state = 1;
+          x.levels.clear();
+        }
         answered = true;
-      } else if (last == x.n - x.k - 1) {
-        walks.push_back({(unsigned long long)lvl.size(), (unsigned long long)x.order_off, last, x.n});
-        for (const LevelRec& l : x.levels) lvl.push_back(l.off);
-        walked.push_back(j);
+      }
+    } else {
+      for (int j = 0; j < G; ++j) {
+        BGraph& x = B.g[j];
+        if (x.state != 0) continue;
+        const int last = (int)x.levels.size() - 1;
+        if (x.levels.back().count == 0) {
+          record_answer(x, false);
+          x.levels.clear();
+          answered = true;
+        } else if (last == x.n - x.k - 1) {
+          walks.push_back({(unsigned long long)lvl.size(), (unsigned long long)x.order_off, last, x.n});
+          for (const LevelRec& l : x.levels) lvl.push_back(l.off);
+          walked.push_back(j);
+        }
       }
     }
     if (!walks.empty()) {
@@ -411,6 +472,10 @@ int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector
   TW_CK(cudaStreamSynchronize(c->stream));
   for (BGraph& x : B.g) {
     if (x.state != 1) continue;
+    if (dm) {
+      (*hst)[x.in_idx] = TW_OK;
+      continue;
+    }
     htw[x.in_idx] = x.tw;
     (*hst)[x.in_idx] = TW_OK;
     if (hord)
@@ -429,7 +494,7 @@ int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::
   NvtxRange range("tw solve_batch graphs=%d", (int)idx.size());
   std::vector<int> small, single;
   for (int i : idx) (graphs[i].n <= 64 ? small : single).push_back(i);
-  int rc = run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single);
+  int rc = run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single, nullptr);
   if (rc) return rc;
   for (int gi : single) {
     const HostGraph& hg = graphs[gi];
@@ -456,6 +521,67 @@ int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::
     if (r2 != TW_OK) htw[gi] = -1;
     (*hst)[gi] = r2;
   }
+  return TW_OK;
+}
+
+// Decide runs of many graphs at their own k: graphs with n <= 64 through the
+// batched kernel, the others (and any the batch evicts) one at a time through
+// the single-graph path, with the Section 3.1 options and pruning turned off
+// so that every graph reports the plain method's level sets.
+int decide_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
+                     const std::vector<int>& kk, std::vector<int>* yes, std::vector<int>* hst,
+                     std::vector<std::vector<unsigned long long>>* size,
+                     std::vector<std::vector<unsigned long long>>* fp_sum,
+                     std::vector<std::vector<unsigned long long>>* fp_xor, tw_stats* st) {
+  NvtxRange range("tw decide_batch graphs=%d", (int)idx.size());
+  std::vector<int> small, single;
+  for (int i : idx) {
+    const int n = graphs[i].n;
+    if (kk[i] >= n - 1) {
+      // the listing's loop is empty: yes with the single level {empty set}
+      (*yes)[i] = 1;
+      (*size)[i].assign(1, 1ull);
+      if (fp_sum) (*fp_sum)[i].assign(1, 0ull);
+      if (fp_xor) (*fp_xor)[i].assign(1, 0ull);
+      (*hst)[i] = TW_OK;
+      continue;
+    }
+    (n <= 64 ? small : single).push_back(i);
+  }
+  BatchDecide dm;
+  dm.k = &kk;
+  dm.yes = yes;
+  dm.size = size;
+  dm.fp_sum = fp_sum;
+  dm.fp_xor = fp_xor;
+  std::vector<int64_t> order_off(graphs.size(), 0);
+  std::vector<int> htw(graphs.size(), -1);
+  int rc = run_batch(c, graphs, small, nullptr, order_off, htw.data(), nullptr, hst, st, &single, &dm);
+  if (rc) return rc;
+  const tw_config saved = c->cfg;
+  c->cfg.clique_skip = c->cfg.disjoint_paths = c->cfg.mmw_prune = 0;
+  c->cfg.fingerprints = fp_sum || fp_xor ? 1 : 0;
+  for (int gi : single) {
+    tw_stats local;
+    std::memset(&local, 0, sizeof(local));
+    int y = 0;
+    const int r2 = decide_graph(c, graphs[gi], kk[gi], &y, nullptr, &local);
+    (*hst)[gi] = r2;
+    if (r2 != TW_OK) continue;
+    (*yes)[gi] = y;
+    (*size)[gi].assign(local.level_size, local.level_size + local.levels);
+    if (fp_sum) (*fp_sum)[gi].assign(local.level_fp_sum, local.level_fp_sum + local.levels);
+    if (fp_xor) (*fp_xor)[gi].assign(local.level_fp_xor, local.level_fp_xor + local.levels);
+    if (st) {
+      st->states_expanded += local.states_expanded;
+      st->candidates += local.candidates;
+      st->generated += local.generated;
+      st->decide_runs += local.decide_runs;
+      st->level_retries += local.level_retries;
+      st->expand_launches += local.expand_launches;
+    }
+  }
+  c->cfg = saved;
   return TW_OK;
 }
 

@@ -96,8 +96,10 @@ int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, 
   return TW_OK;
 }
 
-// One run of Listing 1 at bound k on the graph already uploaded.
-int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R) {
+// One run of Listing 1 at bound k on the graph already uploaded.  With
+// stop_level >= 0 the run ends once that level is built (its answer is then
+// only meaningful when the run reached level n-k-1).
+int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideResult* R, int stop_level) {
   const size_t w = key_bytes(kc);
   // With spill_levels the finished levels go to pinned host memory and the
   // device arena only alternates between the input and the output level.
@@ -141,6 +143,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
   unsigned long long kept_states = 1;  // states of kept levels (keep mode)
   double gen_per_state = 0.0;          // generated pairs per input state of the last level
   for (int i = 0; i <= n - k - 2; ++i) {
+    if (stop_level >= 0 && i >= stop_level) break;
     const LevelRec cur = R->levels[i];
     // Upper bounds on |L_{i+1}|: every state has n-i extensions, and there
     // are C(n, i+1) sets of that size.
@@ -660,7 +663,7 @@ int run_decide_any(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, Decid
     if (rc) return rc;
     if (!bailed) return TW_OK;
   }
-  return run_decide(c, kc, n, k, keep_levels, R);
+  return run_decide(c, kc, n, k, keep_levels, R, -1);
 }
 
 // decide(k) under the context's options (Section 3.1's clique skip and
@@ -752,6 +755,50 @@ int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order,
   int y = R.yes;
   rc = put(c, yes, &y, sizeof(int));
   if (rc) return rc;
+  if (st) {
+    st->seconds = t.seconds();
+    st->kernel_launches = c->launches - launches0;
+  }
+  return TW_OK;
+}
+
+// The sets of one level of decide(k) (run with the context's options, every
+// level kept, stopped after that level), as ceil(n/64) words each.
+int level_keys_graph(tw_ctx* c, const HostGraph& g, int k, int level, uint64_t* keys, uint64_t cap, uint64_t* count,
+                     tw_stats* st) {
+  Timer t;
+  const unsigned long long launches0 = c->launches;
+  if (k < 0 || level < 0 || count == nullptr) return TW_ERR_INVALID;
+  TW_CK(cudaSetDevice(c->device));
+  const KeyClass kc = key_class_for(g.n);
+  int rc = upload_graph(c, g, kc);
+  if (rc) return rc;
+  DecideResult R;
+  bool no = false;
+  if ((rc = prepare_options(c, g, k, kc, &no))) return rc;
+  if (no)
+    immediate_no_result(&R);
+  else if ((rc = run_decide(c, kc, g.n, k, true, &R, level)))
+    return rc;
+  fill_stats(R, k, st, true);
+  const unsigned long long cnt = level < (int)R.levels.size() ? R.levels[level].count : 0ull;
+  if ((rc = put(c, count, &cnt, sizeof(cnt)))) return rc;
+  if (cnt > cap) return TW_ERR_CAPACITY;
+  if (cnt > 0) {
+    if (keys == nullptr) return TW_ERR_INVALID;
+    const LevelRec& lr = R.levels[level];
+    const size_t w = key_bytes(kc);
+    const char* src = lr.hkeys ? lr.hkeys : static_cast<const char*>(c->keys.ptr) + lr.off * w;
+    if (kc == kKey32) {
+      // 32-bit states widen to the ABI's 64-bit words (the table is free now)
+      if ((rc = grow(c, &c->table, (size_t)cnt * 8, 0))) return rc;
+      TW_LAUNCH(c, launch_widen32(reinterpret_cast<const uint32_t*>(src), static_cast<unsigned long long*>(c->table.ptr),
+                                  cnt, c->stream));
+      src = static_cast<const char*>(c->table.ptr);
+    }
+    if ((rc = put_from_device(c, keys, src, (size_t)cnt * (size_t)g.words * 8))) return rc;
+  }
+  TW_CK(cudaStreamSynchronize(c->stream));
   if (st) {
     st->seconds = t.seconds();
     st->kernel_launches = c->launches - launches0;

@@ -144,6 +144,14 @@ __global__ void clear_kernel(uint4* __restrict__ t, size_t n16, LevelCounters* c
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) t[i] = ones;
 }
 
+// ------------------------------------------------------------- widening
+__global__ void widen32_kernel(const uint32_t* __restrict__ src, unsigned long long* __restrict__ dst,
+                               unsigned long long count) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    dst[i] = src[i];
+}
+
 // ------------------------------------------------------------ fingerprints
 template <class K>
 __global__ void fingerprint_kernel(const K* __restrict__ keys, unsigned long long count, LevelCounters* ctr) {
@@ -269,6 +277,12 @@ cudaError_t launch_expand(const ExpandLaunch& a, cudaStream_t s) {
 cudaError_t launch_clear(void* table, size_t table_bytes, LevelCounters* ctr, cudaStream_t s) {
   const size_t n16 = table_bytes / 16;
   clear_kernel<<<stream_grid(n16 > 0 ? n16 : 1, 256 * 4), 256, 0, s>>>(static_cast<uint4*>(table), n16, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen32(const uint32_t* src, unsigned long long* dst, unsigned long long count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  widen32_kernel<<<stream_grid(count, 256 * 4), 256, 0, s>>>(src, dst, count);
   return cudaGetLastError();
 }
 

@@ -170,6 +170,8 @@ double binom(int n, int r);
 
 // ---- tw_decide.cu: decide runs, the k sweep, reconstruction
 int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order, tw_stats* st);
+int level_keys_graph(tw_ctx* c, const HostGraph& g, int k, int level, uint64_t* keys, uint64_t cap, uint64_t* count,
+                     tw_stats* st);
 int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]);
 int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int32_t* td_parent, uint64_t* td_bags,
                 tw_stats* st, int k_first);
@@ -180,6 +182,11 @@ int solve_hinted(tw_ctx* c, const HostGraph& g, float hint, int* tw_out, std::ve
 int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
                     const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
                     std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st);
+int decide_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
+                     const std::vector<int>& kk, std::vector<int>* yes, std::vector<int>* hst,
+                     std::vector<std::vector<unsigned long long>>* size,
+                     std::vector<std::vector<unsigned long long>>* fp_sum,
+                     std::vector<std::vector<unsigned long long>>* fp_xor, tw_stats* st);
 int load_batch(const uint64_t* adj_concat, const int32_t* n, const int64_t* row_offset, int num_graphs,
                std::vector<int32_t>* hn, std::vector<int64_t>* hoff, std::vector<uint64_t>* hadj);
 

@@ -51,6 +51,9 @@ cudaError_t launch_expand(const ExpandLaunch& a, cudaStream_t s);
 // Sets every slot of a table to the empty key (all ones) and zeroes ctr.
 cudaError_t launch_clear(void* table, size_t table_bytes, LevelCounters* ctr, cudaStream_t s);
 
+// dst[i] = src[i] zero-extended, i < count (32-bit states in 64-bit words).
+cudaError_t launch_widen32(const uint32_t* src, unsigned long long* dst, unsigned long long count, cudaStream_t s);
+
 // Adds the fingerprints of count keys into ctr->fp_sum / fp_xor.
 cudaError_t launch_fingerprint(KeyClass kc, const void* keys, unsigned long long count,
                                LevelCounters* ctr, cudaStream_t s);
@@ -178,6 +181,11 @@ cudaError_t launch_expand_batch(const BatchSeg* segs, const unsigned long long* 
 cudaError_t launch_copy_segments(const CopySeg* segs, int nseg, const unsigned long long* src_keys,
                                  const uint32_t* src_par, unsigned long long* dst_keys, uint32_t* dst_par,
                                  cudaStream_t s);
+// out[2s], out[2s+1] += sum and xor of the fingerprints of keys
+// [segs[s].src_off, segs[s].src_off + segs[s].count) (u64 keys); out zeroed
+// by the caller.
+cudaError_t launch_fingerprint_segments(const CopySeg* segs, int nseg, const unsigned long long* keys,
+                                        unsigned long long* out, cudaStream_t s);
 cudaError_t launch_walk_batch(const WalkSeg* walks, int nwalk, const unsigned long long* level_off,
                               const unsigned long long* keys, const uint32_t* par, int32_t* orders, cudaStream_t s);
 

@@ -82,9 +82,13 @@ def lib():
     L.tw_destroy.argtypes = [_vp]
     L.tw_destroy.restype = None
     L.tw_decide.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.POINTER(Stats)]
+    L.tw_decide_level.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_uint64,
+                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Stats)]
     L.tw_decide_u32.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.POINTER(Stats)]
     L.tw_solve.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.POINTER(Stats)]
     L.tw_solve_batch.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.POINTER(Stats)]
+    L.tw_decide_batch.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                                  ctypes.POINTER(Stats)]
     L.tw_bounds.argtypes = [_vp, _vp, ctypes.c_int, _vp]
     L.tw_features_batch.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]
     L.tw_mlp_forward.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
@@ -193,6 +197,28 @@ class Context:
                 raise err
         return {"status": rc, "yes": bool(yes.value == 1), "order": order, "stats": st.as_dict()}
 
+    def decide_level(self, adj, k: int, level: int, n: Optional[int] = None, keys_out=None):
+        """The sets of level ``level`` of decide(k) as a (count, ceil(n/64))
+        uint64 array (unordered).  keys_out (host array or device tensor of
+        at least count * ceil(n/64) words) is used when given; otherwise a host
+        array is sized from a first call that returns the count only."""
+        rows = rows_u64(adj)
+        n = len(adj) if n is None else n
+        w = max(1, (n + 63) // 64)
+        cnt = ctypes.c_uint64(0)
+        st = Stats()
+        if keys_out is None:
+            rc = lib().tw_decide_level(self._h, _ptr(rows), n, k, level, None, 0, ctypes.byref(cnt),
+                                       ctypes.byref(st))
+            if rc not in (TW_OK, TW_ERR_CAPACITY):
+                _check(rc, "tw_decide_level")
+            keys_out = np.zeros((max(1, int(cnt.value)), w), np.uint64)
+        cap = (keys_out.numel() if hasattr(keys_out, "numel") else keys_out.size) // w
+        rc = lib().tw_decide_level(self._h, _ptr(rows), n, k, level, _ptr(keys_out), cap, ctypes.byref(cnt),
+                                   ctypes.byref(st))
+        _check(rc, "tw_decide_level")
+        return {"keys": keys_out[: int(cnt.value)], "count": int(cnt.value), "stats": st.as_dict()}
+
     def decide_u32(self, adj_rows_u32: np.ndarray, n: int, k: int, want_order: bool = False):
         yes = ctypes.c_int(-1)
         st = Stats()
@@ -231,6 +257,24 @@ class Context:
                                   _ptr(status), _ptr(hint), ctypes.byref(st))
         return {"status": rc, "tw": tw, "per_graph_status": status, "orders": orders, "n": ns,
                 "stats": st.as_dict()}
+
+    def decide_batch(self, graphs: Sequence, k, fingerprints: bool = True):
+        """decide(k[g]) for every graph through the batched kernel: answers,
+        per-graph level sizes (and fingerprints) of each run."""
+        adj, ns, offs = graphgen.concat_rows_u64(graphs)
+        G = len(graphs)
+        kk = np.ascontiguousarray(k, dtype=np.int32)
+        yes = np.full(G, -1, np.int32)
+        status = np.full(G, -1, np.int32)
+        L = MAX_N + 1
+        ls = np.zeros((G, L), np.uint64)
+        fs = np.zeros((G, L), np.uint64) if fingerprints else None
+        fx = np.zeros((G, L), np.uint64) if fingerprints else None
+        st = Stats()
+        rc = lib().tw_decide_batch(self._h, _ptr(adj), _ptr(ns), _ptr(offs), G, _ptr(kk), _ptr(yes), _ptr(status),
+                                   _ptr(ls), _ptr(fs), _ptr(fx), ctypes.byref(st))
+        return {"status": rc, "yes": yes, "per_graph_status": status, "level_size": ls, "fp_sum": fs,
+                "fp_xor": fx, "stats": st.as_dict()}
 
     # -------------------------------------------------------------- bounds
     def bounds(self, adj) -> np.ndarray:

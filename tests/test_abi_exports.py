@@ -39,7 +39,7 @@ def test_status_strings_without_gpu():
     from paper_1709_09990_gb300 import native
     assert native.strerror(0) == "ok"
     assert "memory cap" in native.strerror(2)
-    assert native.lib().tw_abi_version() == 2
+    assert native.lib().tw_abi_version() == 3
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):

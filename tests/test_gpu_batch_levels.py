@@ -1,0 +1,83 @@
+"""Per-graph wavefront parity of the batched kernel (tw_decide_batch).
+
+tw_solve_batch reports only treewidths and orderings; tw_decide_batch runs
+decide(k) of many graphs through the same batched kernel and reports each
+graph's level sizes and fingerprints, so the batch path is held to the same
+bar as the single-graph path: every level of every run equal to the oracle's
+(Section 3.1).  The graphs are the graphs with n <= 30 among the first 400
+of the 4096-graph batch workload (185 graphs; the larger ones include runs of
+10^9 states and more), at k = tw and k = tw - 1 (a yes run and a no run
+each).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_09990_gb300 import graphgen as gg
+from tests.gpu_util import context
+
+pytestmark = pytest.mark.gpu
+
+ORACLE_STATES = 400_000  # runs the oracle repeats here (a few seconds each)
+
+
+def _rows(res, g):
+    """Graph g's levels from the zero-padded rows: a yes run ends at its last
+    non-empty level, a no run one level later, at its first empty level."""
+    sizes = res["level_size"][g].tolist()
+    last = max(i for i, x in enumerate(sizes) if x)
+    if res["yes"][g] == 0:
+        last += 1
+    return sizes[: last + 1], res["fp_sum"][g][: last + 1].tolist(), res["fp_xor"][g][: last + 1].tolist()
+
+
+def test_batch_levels_match_oracle_and_single_graph_path():
+    graphs = [a for a in gg.batch_graphs(400) if len(a) <= 30]
+    with context(fingerprints=True) as ctx:
+        sol = ctx.solve_batch(graphs, want_orders=False)
+        assert np.all(sol["per_graph_status"] == 0)
+        tw = sol["tw"]
+        ks = np.concatenate([tw, np.maximum(tw - 1, 0)]).astype(np.int32)
+        twice = graphs + graphs
+        res = ctx.decide_batch(twice, ks)
+        assert res["status"] == 0 and np.all(res["per_graph_status"] == 0)
+        checked_oracle = 0
+        for g, adj in enumerate(twice):
+            k = int(ks[g])
+            sizes, fs, fx = _rows(res, g)
+            single = ctx.decide(adj, k=k)
+            st = single["stats"]
+            assert bool(res["yes"][g]) == single["yes"], (g, k)
+            assert sizes == st["level_size"], (g, k)
+            assert fs == st["fp_sum"] and fx == st["fp_xor"], (g, k)
+            assert bool(res["yes"][g]) == (k >= int(tw[g % len(graphs)])), (g, k)
+            if sum(sizes) <= ORACLE_STATES:
+                exp = oracle.decide(adj, k)
+                assert sizes == exp["level_size"], (g, k)
+                assert fs == exp["fp_sum"] and fx == exp["fp_xor"], (g, k)
+                checked_oracle += 1
+        assert checked_oracle >= 150
+
+
+def test_batch_levels_edge_cases():
+    # n > 64 (the single-graph path inside the batch call: the path P_70 at
+    # k = 1, |L_i| = i + 1, and at k = 0, where L_1 is empty), k >= n-1 (the
+    # single level {empty set}), an empty first level (K_7 at k = 2), n = 1
+    graphs = [gg.path(70), gg.path(70), gg.complete(7), gg.workload_gnp20(), [0], gg.path(9)]
+    ks = np.array([1, 0, 2, 25, 0, 1], np.int32)
+    with context(fingerprints=True) as ctx:
+        res = ctx.decide_batch(graphs, ks)
+        assert res["status"] == 0
+        for g, adj in enumerate(graphs):
+            k = int(ks[g])
+            sizes, fs, fx = _rows(res, g)
+            if k >= len(adj) - 1:
+                assert res["yes"][g] == 1 and sizes == [1] and fs == [0]
+                continue
+            exp = oracle.decide(adj, k)
+            assert bool(res["yes"][g]) == exp["yes"], g
+            assert sizes == exp["level_size"] and fs == exp["fp_sum"] and fx == exp["fp_xor"], g
+        assert _rows(res, 0)[0] == list(range(1, 70))
+        # a negative bound is refused for that graph only
+        bad = ctx.decide_batch(graphs[:3], np.array([-1, 0, 2], np.int32))
+        assert bad["per_graph_status"].tolist() == [1, 0, 0]

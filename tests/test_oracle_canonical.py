@@ -116,3 +116,22 @@ def test_canonical_count_bounds():
             assert sum(d["level_size"][1:]) <= d["canonical"] <= d["feasible"]
             plain = oracle.decide(adj, k)
             assert plain["level_size"] == d["level_size"] and plain["feasible"] == d["feasible"]
+
+
+def test_oracle_level_keys_are_the_brute_force_sets():
+    # the sets the oracle exports for element-wise GPU checks are the whole
+    # level sets of the plain-Python brute force, level by level
+    for adj in _small_graphs()[::3]:
+        n = len(adj)
+        for k in range(n):
+            full, _ = _levels(adj, k, False)
+            for i, lvl in enumerate(full):
+                keys = oracle.level_keys(adj, k, i)
+                assert [int(r[0]) for r in keys] == sorted(lvl), (adj, k, i)
+            assert len(oracle.level_keys(adj, k, len(full))) == 0
+    # two words per set beyond 64 vertices: the star K_{1,69} at k = 1
+    star = gg.star(70)
+    keys = oracle.level_keys(star, 1, 2)
+    assert keys.shape == (math.comb(69, 2), 2)
+    got = {int(r[0]) | (int(r[1]) << 64) for r in keys}
+    assert got == {(1 << a) | (1 << b) for a in range(1, 70) for b in range(a + 1, 70)}

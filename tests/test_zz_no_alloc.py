@@ -116,3 +116,32 @@ def test_static_limits_are_reported():
     rc = f(start.data_ptr(), 1, rows.data_ptr(), 20, 8, out.data_ptr(), pred.data_ptr(), 3,
            ctypes.byref(cnt), stream.cuda_stream)
     assert rc == 2 and int(cnt.value) == 18
+
+
+def test_static_small_buffer_still_counts_exactly_and_rejects_the_full_set():
+    torch = pytest.importorskip("torch")
+    from paper_1709_09990_gb300 import native
+    f = _entry()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=0)
+    adj = gg.workload_gnp20()
+    rows = torch.from_numpy(gg.to_rows_u64(adj).reshape(-1).astype(np.int64)).to(dev)
+    with native.Context(device=0) as ctx:
+        lvl3 = ctx.decide_level(adj, k=8, level=3)["keys"]
+        n4 = ctx.decide_level(adj, k=8, level=4)["count"]
+    assert n4 > 1024  # more states than the table a 3-state buffer is given
+    inp = torch.from_numpy(lvl3.reshape(-1).astype(np.int64)).to(dev)
+    out = torch.empty(64, dtype=torch.int64, device=dev)
+    pred = torch.empty(64, dtype=torch.uint8, device=dev)
+    cnt = ctypes.c_uint64(0)
+    rc = f(inp.data_ptr(), inp.numel(), rows.data_ptr(), 20, 8, out.data_ptr(), pred.data_ptr(), 3,
+           ctypes.byref(cnt), stream.cuda_stream)
+    assert rc == 2 and int(cnt.value) == n4
+    # n = 64: a 63-vertex input set would extend to the all-ones set, the
+    # table's empty marker, so the call is refused
+    path = gg.path(64)
+    prow = torch.from_numpy(gg.to_rows_u64(path).reshape(-1).astype(np.int64)).to(dev)
+    big = torch.tensor([np.int64(-2)], dtype=torch.int64, device=dev)  # every vertex but 0
+    rc = f(big.data_ptr(), 1, prow.data_ptr(), 64, 1, out.data_ptr(), pred.data_ptr(), 64,
+           ctypes.byref(cnt), stream.cuda_stream)
+    assert rc == 1
