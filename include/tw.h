@@ -111,6 +111,34 @@ typedef struct {
                              reads the host copies in place.  Forces the host-
                              driven level loop.  Results are unchanged.  A failed
                              host allocation is TW_ERR_CAPACITY.                  */
+  int out_of_core;        /* 1 = a decide run that needs no ordering goes on when a
+                             level or its table would exceed mem_cap_bytes
+                             (Section 4.2's list capacity; the Conclusions' future
+                             work), instead of returning TW_ERR_CAPACITY: the
+                             table is built in slices, one hash range at a time,
+                             each slice small enough for the cap (the level's
+                             search repeats once per slice), and a level that
+                             does not fit the device is written to pinned host
+                             memory (Grace memory over NVLink-C2C on GB300) and
+                             read from there by the next level.  Results are
+                             unchanged.  tw_decide without order, tw_decide_level
+                             and the decide runs of tw_solve without outputs use
+                             it; a failed host allocation is TW_ERR_CAPACITY.    */
+  int fused_states;       /* tw_solve / tw_decide on graphs with n <= 64 first run
+                             the whole k sweep, walk and tree decomposition in one
+                             cooperative launch (grid barriers between levels)
+                             whose level arena holds this many states; a run
+                             whose levels outgrow it goes on with the level loop
+                             from the k it reached.  0 = 2^20 states (the
+                             default), -1 = never.  Not used with clique_skip,
+                             disjoint_paths, mmw_prune or spill_levels.  Results
+                             are unchanged.                                      */
+  int batch_kernel;       /* tw_solve_batch / tw_decide_batch: 0 = one persistent
+                             launch for the whole batch, each block solving one
+                             graph at a time from a device queue (the default);
+                             1 = level-synchronous steps, one launch per step for
+                             the current level of every running graph.  Results
+                             are unchanged.                                      */
   int reserved[1];        /* must be zero                                         */
 } tw_config;
 

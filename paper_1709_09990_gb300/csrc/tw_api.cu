@@ -125,11 +125,15 @@ void tw_destroy(tw_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (DevBuf* b : {&c->keys, &c->pred, &c->table, &c->small, &c->scratch, &c->cand_key, &c->cand_v, &c->part_meta})
+  for (DevBuf* b : {&c->keys, &c->pred, &c->table, &c->small, &c->scratch, &c->cand_key, &c->cand_v, &c->part_meta,
+                    &c->ooc_keys, &c->fused})
     if (b->ptr) cudaFree(b->ptr);
   for (const tw_ctx::HostChunk& ch : c->host_chunks) cudaFreeHost(ch.ptr);
+  for (const tw_ctx::HostChunk& ch : c->ooc_host)
+    if (ch.ptr) cudaFreeHost(ch.ptr);
   if (c->d_ctr) cudaFree(c->d_ctr);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_fused) cudaFreeHost(c->h_fused);
   for (auto& e : c->graphs) {
     cudaGraphExecDestroy(e.exec);
     for (cudaEvent_t v : e.ev) cudaEventDestroy(v);

@@ -486,6 +486,185 @@ int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector
   return TW_OK;
 }
 
+// ---------------------------------------------------------------- persistent
+//
+// The default batched path: one launch of batch_solve_kernel (tw_batch_solve.cu)
+// for all graphs with n <= 64; each block solves one graph at a time from a
+// device queue.  Graphs are queued largest n first so that long solves start
+// early.  A graph whose levels outgrow a block's workspace is returned in
+// *evicted for the single-graph path.
+// Device allocations of one call, freed (after the stream) on return.
+struct DevMem {
+  tw_ctx* c;
+  std::vector<void*> p;
+  explicit DevMem(tw_ctx* cc) : c(cc) {}
+  ~DevMem() {
+    cudaStreamSynchronize(c->stream);
+    for (void* x : p) cudaFree(x);
+    cudaGetLastError();
+  }
+  template <class X>
+  int get(X** out, size_t count) {
+    void* v = nullptr;
+    if (cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) {
+      cudaGetLastError();
+      return TW_ERR_CAPACITY;
+    }
+    p.push_back(v);
+    *out = static_cast<X*>(v);
+    return TW_OK;
+  }
+};
+
+int run_batch_persistent(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
+                         const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
+                         std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st, std::vector<int>* evicted,
+                         const BatchDecide* dm) {
+  const int G = (int)idx.size();
+  if (G == 0) return TW_OK;
+  NvtxRange range("tw batch persistent graphs=%d", G);
+  std::vector<int> q(idx);
+  std::stable_sort(q.begin(), q.end(), [&](int a, int b) { return graphs[a].n > graphs[b].n; });
+  std::vector<unsigned long long> rows((size_t)G * 64, 0ull);
+  std::vector<int32_t> ns(G), kst(G), lbv(G);
+  std::vector<int64_t> offs(G), ooff(G);
+  int64_t total_n = 0;
+  for (int j = 0; j < G; ++j) {
+    const HostGraph& hg = graphs[q[j]];
+    for (int r = 0; r < hg.n; ++r) rows[(size_t)j * 64 + r] = hg.rows[r];
+    ns[j] = hg.n;
+    offs[j] = (int64_t)j * 64;
+    ooff[j] = order_off[q[j]];
+    total_n = std::max<int64_t>(total_n, ooff[j] + hg.n);
+  }
+  const int warps = 4;
+  const int blocks = batch_solve_blocks(warps);
+  // workspace: per block A keys and predecessor bytes, two tables of 2A slots
+  const size_t room = c->mem_cap > total_bytes(c) ? c->mem_cap - total_bytes(c) : 0;
+  const size_t budget = std::min<size_t>(room / 4, 32ull << 30);
+  unsigned long long A = 1ull << 19;
+  while (A > 4096 && (size_t)blocks * (A * 41 + 4096) > budget) A >>= 1;
+  const unsigned long long T = 2 * A;
+  DevMem mem(c);
+  BatchSolveArgs a{};
+  unsigned long long* d_adj = nullptr;
+  int32_t *d_n = nullptr, *d_lb = nullptr, *d_k = nullptr, *d_b = nullptr;
+  int64_t *d_off = nullptr, *d_ooff = nullptr;
+  int rc;
+  if ((rc = mem.get(&d_adj, rows.size())) || (rc = mem.get(&d_n, G)) || (rc = mem.get(&d_lb, G)) ||
+      (rc = mem.get(&d_k, G)) || (rc = mem.get(&d_b, (size_t)G * 4)) || (rc = mem.get(&d_off, G)) ||
+      (rc = mem.get(&d_ooff, G)))
+    return rc;
+  TW_CK(cudaMemcpyAsync(d_adj, rows.data(), rows.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(cudaMemcpyAsync(d_n, ns.data(), (size_t)G * 4, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(cudaMemcpyAsync(d_off, offs.data(), (size_t)G * 8, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(cudaMemcpyAsync(d_ooff, ooff.data(), (size_t)G * 8, cudaMemcpyHostToDevice, c->stream));
+  TW_LAUNCH(c, launch_bounds(d_adj, d_n, d_off, G, d_b, nullptr, c->stream));
+  std::vector<int32_t> b((size_t)G * 4);
+  TW_CK(cudaMemcpyAsync(b.data(), d_b, b.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaStreamSynchronize(c->stream));
+  for (int j = 0; j < G; ++j) {
+    const int gi = q[j], n = ns[j];
+    lbv[j] = std::max(b[4 * j], b[4 * j + 1]);
+    int k0 = lbv[j];
+    if (hint) k0 = (int)std::lround((*hint)[gi]);
+    kst[j] = std::min(std::max(k0, lbv[j]), n - 1);
+    if (dm) kst[j] = (*dm->k)[gi];
+  }
+  TW_CK(cudaMemcpyAsync(d_lb, lbv.data(), (size_t)G * 4, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(cudaMemcpyAsync(d_k, kst.data(), (size_t)G * 4, cudaMemcpyHostToDevice, c->stream));
+  a.adj = d_adj;
+  a.n = d_n;
+  a.lb = d_lb;
+  a.k_start = d_k;
+  a.num_graphs = G;
+  a.decide_mode = dm ? 1 : 0;
+  a.max_probes = kBatchProbes;
+  a.load_pct = 50;
+  a.A = A;
+  a.T = T;
+  unsigned int* d_next = nullptr;
+  unsigned long long* d_tot = nullptr;
+  if ((rc = mem.get(&d_next, 1)) || (rc = mem.get(&d_tot, 4)) || (rc = mem.get(&a.arena, (size_t)blocks * A)) ||
+      (rc = mem.get(&a.pred, (size_t)blocks * A)) || (rc = mem.get(&a.tables, (size_t)blocks * 2 * T)) ||
+      (rc = mem.get(&a.ctr, (size_t)blocks)) || (rc = mem.get(&a.level_off, (size_t)blocks * 130)) ||
+      (rc = mem.get(&a.level_cnt, (size_t)blocks * 130)) || (rc = mem.get(&a.tw, G)) || (rc = mem.get(&a.status, G)))
+    return rc;
+  TW_CK(cudaMemsetAsync(d_next, 0, 4, c->stream));
+  TW_CK(cudaMemsetAsync(d_tot, 0, 32, c->stream));
+  a.next_graph = d_next;
+  a.totals = d_tot;
+  a.order_off = d_ooff;
+  if (hord && !dm && (rc = mem.get(&a.orders, (size_t)std::max<int64_t>(total_n, 1)))) return rc;
+  if (dm) {
+    if ((rc = mem.get(&a.yes, G)) || (rc = mem.get(&a.last, G)) || (rc = mem.get(&a.level_size, (size_t)G * 129)))
+      return rc;
+    TW_CK(cudaMemsetAsync(a.level_size, 0, (size_t)G * 129 * 8, c->stream));
+    if (dm->fp_sum) {
+      if ((rc = mem.get(&a.fp_sum, (size_t)G * 129)) || (rc = mem.get(&a.fp_xor, (size_t)G * 129))) return rc;
+      TW_CK(cudaMemsetAsync(a.fp_sum, 0, (size_t)G * 129 * 8, c->stream));
+      TW_CK(cudaMemsetAsync(a.fp_xor, 0, (size_t)G * 129 * 8, c->stream));
+    }
+  }
+  TW_LAUNCH(c, launch_batch_solve(a, blocks, warps, c->stream));
+  if (st) st->expand_launches += 1;
+  std::vector<int32_t> htw_p(G), hst_p(G);
+  unsigned long long tot[4];
+  TW_CK(cudaMemcpyAsync(hst_p.data(), a.status, (size_t)G * 4, cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaMemcpyAsync(htw_p.data(), a.tw, (size_t)G * 4, cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaMemcpyAsync(tot, d_tot, 32, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<int32_t> dord;
+  if (a.orders) {
+    dord.resize((size_t)total_n);
+    TW_CK(cudaMemcpyAsync(dord.data(), a.orders, dord.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+  }
+  std::vector<int32_t> hy, hl;
+  std::vector<unsigned long long> hls, hfs, hfx;
+  if (dm) {
+    hy.resize(G);
+    hl.resize(G);
+    hls.resize((size_t)G * 129);
+    TW_CK(cudaMemcpyAsync(hy.data(), a.yes, (size_t)G * 4, cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaMemcpyAsync(hl.data(), a.last, (size_t)G * 4, cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaMemcpyAsync(hls.data(), a.level_size, hls.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (a.fp_sum) {
+      hfs.resize((size_t)G * 129);
+      hfx.resize((size_t)G * 129);
+      TW_CK(cudaMemcpyAsync(hfs.data(), a.fp_sum, hfs.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaMemcpyAsync(hfx.data(), a.fp_xor, hfx.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  TW_CK(cudaStreamSynchronize(c->stream));
+  if (st) {
+    st->states_expanded += tot[0];
+    st->candidates += tot[1];
+    st->generated += tot[2];
+    st->decide_runs += tot[3];
+  }
+  for (int j = 0; j < G; ++j) {
+    const int gi = q[j];
+    if (hst_p[j] != 0) {
+      evicted->push_back(gi);
+      continue;
+    }
+    (*hst)[gi] = TW_OK;
+    if (dm) {
+      (*dm->yes)[gi] = hy[j];
+      const int L = hl[j] + 1;
+      (*dm->size)[gi].assign(hls.begin() + (size_t)j * 129, hls.begin() + (size_t)j * 129 + L);
+      if (dm->fp_sum) {
+        (*dm->fp_sum)[gi].assign(hfs.begin() + (size_t)j * 129, hfs.begin() + (size_t)j * 129 + L);
+        (*dm->fp_xor)[gi].assign(hfx.begin() + (size_t)j * 129, hfx.begin() + (size_t)j * 129 + L);
+      }
+      continue;
+    }
+    htw[gi] = htw_p[j];
+    if (hord && a.orders)
+      for (int v = 0; v < ns[j]; ++v) (*hord)[ooff[j] + v] = dord[ooff[j] + v];
+  }
+  return TW_OK;
+}
+
 // Graphs with n <= 64 go through the batched kernel; graphs it evicts and
 // graphs with n > 64 are solved one at a time by the single-graph path.
 int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
@@ -494,7 +673,9 @@ int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::
   NvtxRange range("tw solve_batch graphs=%d", (int)idx.size());
   std::vector<int> small, single;
   for (int i : idx) (graphs[i].n <= 64 ? small : single).push_back(i);
-  int rc = run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single, nullptr);
+  int rc = c->cfg.batch_kernel == 1 ? run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single, nullptr)
+                                    : run_batch_persistent(c, graphs, small, hint, order_off, htw, hord, hst, st, &single,
+                                                           nullptr);
   if (rc) return rc;
   for (int gi : single) {
     const HostGraph& hg = graphs[gi];
@@ -556,7 +737,9 @@ int decide_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std:
   dm.fp_xor = fp_xor;
   std::vector<int64_t> order_off(graphs.size(), 0);
   std::vector<int> htw(graphs.size(), -1);
-  int rc = run_batch(c, graphs, small, nullptr, order_off, htw.data(), nullptr, hst, st, &single, &dm);
+  int rc = c->cfg.batch_kernel == 1
+               ? run_batch(c, graphs, small, nullptr, order_off, htw.data(), nullptr, hst, st, &single, &dm)
+               : run_batch_persistent(c, graphs, small, nullptr, order_off, htw.data(), nullptr, hst, st, &single, &dm);
   if (rc) return rc;
   const tw_config saved = c->cfg;
   c->cfg.clique_skip = c->cfg.disjoint_paths = c->cfg.mmw_prune = 0;

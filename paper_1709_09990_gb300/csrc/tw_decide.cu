@@ -14,6 +14,7 @@
 // A level whose table or output list turns out too small is cleared and run
 // again with larger buffers, so no state is ever lost.
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cmath>
@@ -96,6 +97,244 @@ int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, 
   return TW_OK;
 }
 
+// ---- out-of-core levels (tw_config.out_of_core) ------------------------------
+//
+// A decide run without ordering keeps only two levels: the one being expanded
+// and the one being built.  When one of them or the level's table would not
+// fit the memory cap, the run goes on here:
+//  * the new level goes to the device arena if it fits there next to the
+//    input level and a table slice of reasonable size, else to one of two
+//    pinned, device-mapped host buffers (the one not holding the input), and
+//    the next level reads it from there;
+//  * the level's table is split into P hash ranges: each pass empties a slice
+//    that fits what the cap leaves, expands the whole input level and inserts
+//    only the pairs whose hash falls in its range (the ranged kernel), so the
+//    passes together insert every pair once.
+// Level sets, sizes and counters are those of the in-memory run; the input is
+// read and searched once per pass.
+
+// Host buffer hb of the context, grown to at least bytes; *dptr is its
+// device-side address.
+int ooc_host_buffer(tw_ctx* c, int hb, size_t bytes, char** dptr) {
+  tw_ctx::HostChunk& ch = c->ooc_host[hb];
+  if (ch.bytes < bytes) {
+    // both buffers together stay within 85% of the host's physical memory
+    const size_t phys = (size_t)sysconf(_SC_PHYS_PAGES) * (size_t)sysconf(_SC_PAGESIZE);
+    if (bytes + c->ooc_host[1 - hb].bytes > phys / 20 * 17) return TW_ERR_CAPACITY;
+    if (ch.ptr) {
+      TW_CK(cudaStreamSynchronize(c->stream));
+      cudaFreeHost(ch.ptr);
+      ch = {nullptr, nullptr, 0};
+    }
+    const size_t gib = size_t(1) << 30;
+    const size_t want = (bytes + gib - 1) / gib * gib;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, want, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      return TW_ERR_CAPACITY;
+    }
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(p);
+      return TW_ERR_CUDA;
+    }
+    ch = {static_cast<char*>(p), static_cast<char*>(d), want};
+  }
+  *dptr = ch.dptr;
+  return TW_OK;
+}
+
+void release(tw_ctx* c, DevBuf* b) {
+  if (!b->ptr) return;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(b->ptr);
+  b->ptr = nullptr;
+  b->bytes = 0;
+}
+
+// Allocates b with exactly bytes (rounded up to 256); false when the cap or
+// the device refuses.
+bool alloc_exact(tw_ctx* c, DevBuf* b, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (total_bytes(c) - b->bytes + bytes > c->mem_cap) return false;
+  release(c, b);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  b->ptr = p;
+  b->bytes = bytes;
+  return true;
+}
+
+// Continues decide(k) out of core from the last level of R (on the device in
+// the level arena at its offset).  Levels live in one of two device buffers
+// (the level arena and c->ooc_keys) or one of two host buffers; the new level
+// goes to the device buffer that does not hold the input when it fits there
+// with a table slice, else to the host buffer that does not hold the input.
+// stop_level as in run_decide.
+int run_decide_ooc(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, int stop_level) {
+  NvtxRange range("tw decide out of core n=%d k=%d", n, k);
+  const size_t w = key_bytes(kc);
+  SmallLayout L;
+  release(c, &c->pred);
+  release(c, &c->cand_key);
+  release(c, &c->cand_v);
+  DevBuf* dev[2] = {&c->keys, &c->ooc_keys};
+  const int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 75;
+  const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
+  const size_t margin = std::min<size_t>(64ull << 20, c->mem_cap / 16);
+  int in_dev = 0, in_host = -1;  // where the input level is (device or host buffer)
+  for (int i = (int)R->levels.size() - 1; i <= n - k - 2; ++i) {
+    if (stop_level >= 0 && i >= stop_level) break;
+    const LevelRec cur = R->levels[i];
+    if (cur.count == 0) break;
+    const double bound = std::min((double)cur.count * (double)(n - i), binom(n, i + 1)) + 1.0;
+    double est = (double)cur.count;
+    if (i > 0 && R->levels[i - 1].count > 0) {
+      double r = (double)cur.count / (double)R->levels[i - 1].count;
+      r = std::min(std::max(r, 0.25), (double)(n - i));
+      est = (double)cur.count * r;
+    }
+    double out_est = std::min(bound, est * 1.10 + 4096.0);
+    const char* in_ptr =
+        in_host >= 0 ? c->ooc_host[in_host].dptr : static_cast<char*>(dev[in_dev]->ptr) + cur.off * w;
+    if (in_host >= 0) {
+      release(c, dev[0]);
+      release(c, dev[1]);
+    }
+    LevelRec nxt;
+    unsigned long long generated = 0;
+    int passes = 0, out_dev = -1, out_host = -1;
+    float ms_total = 0.f;
+    for (int attempt = 0;; ++attempt) {
+      if (attempt > 16) return TW_ERR_CAPACITY;
+      const unsigned long long out_cap = (unsigned long long)std::ceil(out_est);
+      release(c, &c->table);
+      const unsigned long long total_slots =
+          std::max<unsigned long long>(1024ull, (unsigned long long)std::ceil(out_est * 100.0 / load_pct));
+      const size_t table_bytes = (size_t)total_slots * w;
+      const size_t min_slice = std::max<size_t>(std::min<size_t>(512ull << 20, c->mem_cap / 4), table_bytes / 64);
+      // the new level: on the device buffer the input does not use, if it
+      // fits there with a table slice; else in host memory
+      out_dev = in_host >= 0 ? 0 : 1 - in_dev;
+      out_host = -1;
+      release(c, dev[out_dev]);
+      const size_t out_bytes = std::max<size_t>(256, (size_t)out_cap * w);
+      char* out_ptr = nullptr;
+      if (total_bytes(c) + out_bytes + min_slice + margin <= c->mem_cap && alloc_exact(c, dev[out_dev], out_bytes)) {
+        out_ptr = static_cast<char*>(dev[out_dev]->ptr);
+      } else {
+        out_dev = -1;
+        out_host = in_host >= 0 ? 1 - in_host : 0;
+        int rc = ooc_host_buffer(c, out_host, out_bytes, &out_ptr);
+        if (rc) return rc;
+      }
+      // the table: as many hash-range passes as the cap needs
+      const size_t dev_used = total_bytes(c) + margin;
+      if (dev_used + 16384 > c->mem_cap) return TW_ERR_CAPACITY;
+      const size_t slice_budget = c->mem_cap - dev_used;
+      unsigned long long P = std::max<unsigned long long>(1ull, (table_bytes + slice_budget - 1) / slice_budget);
+      unsigned long long slice_slots = 0;
+      size_t slice_bytes = 0;
+      for (;; P *= 2) {  // (more, smaller slices when the device refuses one)
+        if (P > 1024) return TW_ERR_CAPACITY;
+        slice_slots = (total_slots + P - 1) / P + 1024ull;
+        slice_bytes = (size_t)((slice_slots * w + 15) & ~15ull);
+        if (alloc_exact(c, &c->table, slice_bytes)) break;
+      }
+      const bool timed = c->cfg.time_kernels != 0;
+      bool table_full = false;
+      unsigned long long before = 0;
+      LevelCounters h{};
+      ms_total = 0.f;
+      for (unsigned long long r = 0; r < P; ++r) {
+        TW_LAUNCH(c, launch_clear(c->table.ptr, slice_bytes, r == 0 ? c->d_ctr : nullptr, c->stream));
+        ExpandLaunch a;
+        a.kc = kc;
+        a.in_keys = in_ptr;
+        a.n_in = cur.count;
+        a.adj = small_at(c, L.adj);
+        a.n = n;
+        a.k = k;
+        a.table = c->table.ptr;
+        a.table_slots = slice_slots;
+        a.max_probes = max_probes;
+        a.out_keys = out_ptr;
+        a.out_pred = nullptr;
+        a.out_cap = out_cap;
+        a.ctr = c->d_ctr;
+        a.block_threads = 128;
+        a.grid = 0;
+        a.allowed[0] = c->allowed[0];
+        a.allowed[1] = c->allowed[1];
+        a.mmw = 0;
+        a.ranges = P;
+        a.range = r;
+        if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
+        TW_LAUNCH(c, launch_expand(a, c->stream));
+        if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
+        TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+        TW_CK(cudaStreamSynchronize(c->stream));
+        h = *c->h_ctr;
+        if (timed) {
+          float ms = 0.f;
+          TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+          ms_total += ms;
+        }
+        const unsigned long long got = h.out_count - before;
+        before = h.out_count;
+        if ((h.overflow & 2u) || got * 100ull > slice_slots * 90ull) {
+          // this range held more than its slice: more states than estimated
+          table_full = true;
+          const double projected = (double)h.out_count / (double)(r + 1) * (double)P;
+          out_est = std::max(out_est * 1.5, projected * 1.2);
+          break;
+        }
+      }
+      if (attempt > 0) ++R->retries;
+      if (table_full) continue;
+      if (h.overflow & 1u) {
+        out_est = (double)h.out_count;  // exact: every range was inserted completely
+        continue;
+      }
+      nxt.off = 0;
+      nxt.count = h.out_count;
+      nxt.hkeys = out_host >= 0 ? out_ptr : nullptr;
+      generated = h.generated;
+      passes = (int)P;
+      R->peak_bytes = std::max<unsigned long long>(R->peak_bytes, total_bytes(c));
+      break;
+    }
+    R->states_expanded += cur.count;
+    R->candidates += cur.count * (unsigned long long)(n - c->skipped - i);
+    R->generated += generated;
+    R->expand_launches += (unsigned long long)passes;
+    R->expand_seconds += (double)ms_total * 1e-3;
+    R->expand_bytes += (double)(cur.count + generated + 2ull * nxt.count) * (double)w;
+    R->levels.push_back(nxt);
+    const char* out_keys = out_host >= 0 ? c->ooc_host[out_host].dptr : static_cast<char*>(dev[out_dev]->ptr);
+    in_dev = out_dev;
+    in_host = out_host;
+    if (c->cfg.fingerprints) {
+      TW_LAUNCH(c, launch_fingerprint(kc, out_keys, nxt.count, c->d_ctr, c->stream));
+      TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      R->fp_sum.push_back(c->h_ctr->fp_sum);
+      R->fp_xor.push_back(c->h_ctr->fp_xor);
+    }
+    if (nxt.count == 0) break;
+  }
+  const int last = (int)R->levels.size() - 1;
+  R->yes = (last == n - k - 1 && R->levels[last].count > 0) ? 1 : 0;
+  // device level records refer to the level arena (callers read the last
+  // level only): make the buffer that holds the last level the arena
+  if (in_host < 0 && in_dev == 1) std::swap(c->keys, c->ooc_keys);
+  return TW_OK;
+}
+
 // One run of Listing 1 at bound k on the graph already uploaded.  With
 // stop_level >= 0 the run ends once that level is built (its answer is then
 // only meaningful when the run reached level n-k-1).
@@ -104,6 +343,8 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
   // With spill_levels the finished levels go to pinned host memory and the
   // device arena only alternates between the input and the output level.
   const bool spill = keep_levels && c->cfg.spill_levels != 0;
+  // levels or tables beyond the cap continue out of core (no ordering only)
+  const bool ooc = c->cfg.out_of_core != 0 && !keep_levels && !spill && !c->cfg.mmw_prune;
   if (spill) {
     c->host_chunk = 0;
     c->host_used = 0;
@@ -118,8 +359,15 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
   R->fp_sum.assign(1, 0ull);  // fp of the empty set is 0
   R->fp_xor.assign(1, 0ull);
   int rc = grow(c, &c->keys, 64 * w, 0);
-  if (rc) return rc;
-  rc = grow(c, &c->pred, 64, 0);
+  if (rc == TW_OK) rc = grow(c, &c->pred, 64, 0);
+  if (rc == TW_ERR_CAPACITY) {
+    // the buffers of an earlier run fill the cap: its table and its second
+    // level buffer are scratch now
+    release(c, &c->table);
+    release(c, &c->ooc_keys);
+    rc = grow(c, &c->keys, 64 * w, 0);
+    if (rc == TW_OK) rc = grow(c, &c->pred, 64, 0);
+  }
   if (rc) return rc;
   TW_CK(cudaMemsetAsync(c->keys.ptr, 0, w, c->stream));
   R->levels.push_back({0, 1});
@@ -239,10 +487,9 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       const unsigned long long live_end = cur.off + cur.count;  // data to keep on growth
       const size_t table_bytes = (slots * w + 15) & ~size_t(15);
       rc = grow(c, &c->table, table_bytes, 0);
-      if (rc) return rc;
-      rc = grow(c, &c->keys, (size_t)(off + out_cap) * w, (size_t)live_end * w);
-      if (rc) return rc;
-      rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)live_end);
+      if (rc == TW_OK) rc = grow(c, &c->keys, (size_t)(off + out_cap) * w, (size_t)live_end * w);
+      if (rc == TW_OK) rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)live_end);
+      if (rc == TW_ERR_CAPACITY && ooc) return run_decide_ooc(c, kc, n, k, R, stop_level);
       if (rc) return rc;
       TW_LAUNCH(c, launch_clear(c->table.ptr, table_bytes, c->d_ctr, c->stream));
       ExpandLaunch a;
@@ -679,6 +926,142 @@ int decide_with_options(tw_ctx* c, const HostGraph& g, KeyClass kc, int k, bool 
   return run_decide_any(c, kc, g.n, k, keep_levels, R);
 }
 
+// ---- fused small solve (tw_fused.cu) -----------------------------------------
+void fill_stats(const DecideResult& R, int k, tw_stats* st, bool reset_totals);
+
+unsigned long long graph_hash(const HostGraph& g) {
+  unsigned long long h = 0x9e3779b97f4a7c15ull ^ (unsigned long long)g.n;
+  for (uint64_t r : g.rows) {
+    h ^= r + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h *= 0xff51afd7ed558ccdull;
+  }
+  return h;
+}
+
+bool fused_eligible(const tw_ctx* c, const HostGraph& g) {
+  if (g.n > 64 || c->cfg.fused_states < 0 || c->cfg.clique_skip || c->cfg.disjoint_paths || c->cfg.mmw_prune ||
+      c->cfg.spill_levels)
+    return false;
+  const unsigned long long h = graph_hash(g);
+  for (unsigned long long x : c->fused_skip)
+    if (x == h) return false;
+  return true;
+}
+
+// decide(k) for k = k0 .. k_last in one fused launch on the graph already
+// uploaded.  *status: 1 = finished - R describes the last run (the yes run
+// when *answer_k >= 0, with the ordering and tree decomposition in the small
+// buffer); 2 = gave up at k = *bail_k (the runs before it answered no), and
+// the graph is remembered so that later solves skip the fused attempt; 0 =
+// not run (its buffers do not fit the memory cap).
+// Totals of every run go into st.
+int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, DecideResult* R, int* status,
+              int* answer_k, int* bail_k, tw_stats* st) {
+  NvtxRange range("tw fused solve n=%d k0=%d", g.n, k0);
+  const size_t w = key_bytes(kc);
+  const unsigned long long A =
+      c->cfg.fused_states > 0 ? (unsigned long long)c->cfg.fused_states : (1ull << 20);
+  const unsigned long long T = 2 * A + 1024;
+  const size_t st_bytes = (sizeof(FusedState) + 255) & ~size_t(255);
+  const size_t tb = ((size_t)T * 8 + 255) & ~size_t(255);  // sized for 64-bit states
+  const size_t kb = ((size_t)A * 8 + 255) & ~size_t(255);
+  const size_t need = st_bytes + 2 * tb + kb + A;
+  *status = 0;
+  if (c->fused.bytes < need) {
+    int rc = grow(c, &c->fused, need, 0);
+    if (rc == TW_ERR_CAPACITY) return TW_OK;  // no room under the cap: the level loop runs instead
+    if (rc) return rc;
+  }
+  if (!c->h_fused) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_fused), sizeof(FusedState), cudaHostAllocDefault) !=
+        cudaSuccess) {
+      c->h_fused = nullptr;
+      cudaGetLastError();
+      return TW_ERR_CUDA;
+    }
+  }
+  char* base = static_cast<char*>(c->fused.ptr);
+  SmallLayout L;
+  FusedLaunch f;
+  f.kc = kc;
+  f.adj = small_at(c, L.adj);
+  f.adj64 = reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64));
+  f.n = g.n;
+  f.words64 = g.words;
+  f.k0 = k0;
+  f.k_last = k_last;
+  f.max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
+  f.load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
+  f.st = reinterpret_cast<FusedState*>(base);
+  f.table0 = base + st_bytes;
+  f.table1 = base + st_bytes + tb;
+  f.keys = base + st_bytes + 2 * tb;
+  f.pred = reinterpret_cast<uint8_t*>(base + st_bytes + 2 * tb + kb);
+  f.arena_cap = A;
+  f.table_cap = T;
+  f.order = reinterpret_cast<int32_t*>(small_at(c, L.order));
+  f.parent = reinterpret_cast<int32_t*>(small_at(c, L.parent));
+  f.bags = reinterpret_cast<unsigned long long*>(small_at(c, L.bags));
+  TW_CK(cudaMemsetAsync(f.st, 0, sizeof(FusedState), c->stream));
+  const bool timed = c->cfg.time_kernels != 0;
+  if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
+  TW_LAUNCH(c, launch_fused_solve(f, c->stream));
+  if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
+  TW_CK(cudaMemcpyAsync(c->h_fused, f.st, sizeof(FusedState), cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaStreamSynchronize(c->stream));
+  const FusedState& h = *c->h_fused;
+  if (h.error) return TW_ERR_TIMEOUT;  // a grid barrier wait gave up
+  *status = h.status;
+  if (h.status != 1) {
+    *bail_k = h.last;
+    if (c->fused_skip.size() >= 4096) c->fused_skip.clear();
+    c->fused_skip.push_back(graph_hash(g));
+    if (st) {
+      st->states_expanded += h.states_expanded;
+      st->candidates += h.candidates;
+      st->generated += h.generated;
+      st->decide_runs += (unsigned long long)std::max(0, h.last - k0);
+    }
+    return TW_OK;
+  }
+  *answer_k = h.tw;
+  const int last_k = h.tw >= 0 ? h.tw : k_last;
+  R->levels.clear();
+  for (int j = 0; j <= h.last; ++j) R->levels.push_back({h.level_off[j], h.level_cnt[j]});
+  R->yes = h.tw >= 0 ? 1 : 0;
+  R->states_expanded = h.states_expanded;
+  R->candidates = h.candidates;
+  R->generated = h.generated;
+  R->retries = 0;
+  R->peak_bytes = c->fused.bytes;
+  R->expand_launches = 1;
+  R->expand_seconds = 0.0;
+  if (timed) {
+    float ms = 0.f;
+    TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    R->expand_seconds = (double)ms * 1e-3;
+  }
+  unsigned long long out_states = 0;
+  for (int j = 1; j <= h.last; ++j) out_states += h.level_cnt[j];
+  R->expand_bytes = (double)(h.states_expanded + h.generated + 2ull * out_states) * (double)w + (double)out_states;
+  R->fp_sum.assign(1, 0ull);
+  R->fp_xor.assign(1, 0ull);
+  if (c->cfg.fingerprints) {
+    for (int j = 1; j <= h.last; ++j) {
+      TW_CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(LevelCounters), c->stream));
+      TW_LAUNCH(c, launch_fingerprint(kc, static_cast<char*>(f.keys) + h.level_off[j] * w, h.level_cnt[j], c->d_ctr,
+                                      c->stream));
+      TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+      TW_CK(cudaStreamSynchronize(c->stream));
+      R->fp_sum.push_back(c->h_ctr->fp_sum);
+      R->fp_xor.push_back(c->h_ctr->fp_xor);
+    }
+  }
+  fill_stats(*R, last_k, st, false);
+  if (st) st->decide_runs += (unsigned long long)(last_k - k0);  // fill_stats counted one run
+  return TW_OK;
+}
+
 // Backward walk through the kept levels into the device order buffer.
 int reconstruct(tw_ctx* c, KeyClass kc, int n, const DecideResult& R) {
   NvtxRange range("tw walk n=%d levels=%d", n, (int)R.levels.size());
@@ -737,6 +1120,29 @@ int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order,
   int rc = upload_graph(c, g, kc);
   if (rc) return rc;
   DecideResult R;
+  if (fused_eligible(c, g)) {
+    int status = 0, ans = -1, bail_k = -1;
+    tw_stats tmp;
+    std::memset(&tmp, 0, sizeof(tmp));
+    rc = run_fused(c, g, kc, k, k, &R, &status, &ans, &bail_k, &tmp);
+    if (rc) return rc;
+    if (status == 1) {
+      if (R.yes && order) {
+        rc = put_from_device(c, order, small_at(c, SmallLayout().order), (size_t)g.n * 4);
+        if (rc) return rc;
+      }
+      TW_CK(cudaStreamSynchronize(c->stream));
+      fill_stats(R, k, st, true);
+      int y = R.yes;
+      rc = put(c, yes, &y, sizeof(int));
+      if (rc) return rc;
+      if (st) {
+        st->seconds = t.seconds();
+        st->kernel_launches = c->launches - launches0;
+      }
+      return TW_OK;
+    }
+  }
   rc = decide_with_options(c, g, kc, k, order != nullptr, &R);
   if (rc) {
     // the levels completed before the failure are still reported
@@ -762,8 +1168,9 @@ int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order,
   return TW_OK;
 }
 
-// The sets of one level of decide(k) (run with the context's options, every
-// level kept, stopped after that level), as ceil(n/64) words each.
+// The sets of one level of decide(k) (run with the context's options and
+// stopped after that level, so that it is the live output level), as
+// ceil(n/64) words each.
 int level_keys_graph(tw_ctx* c, const HostGraph& g, int k, int level, uint64_t* keys, uint64_t cap, uint64_t* count,
                      tw_stats* st) {
   Timer t;
@@ -778,8 +1185,10 @@ int level_keys_graph(tw_ctx* c, const HostGraph& g, int k, int level, uint64_t* 
   if ((rc = prepare_options(c, g, k, kc, &no))) return rc;
   if (no)
     immediate_no_result(&R);
-  else if ((rc = run_decide(c, kc, g.n, k, true, &R, level)))
+  else if ((rc = run_decide(c, kc, g.n, k, false, &R, level))) {  // the level asked for is the last one built
+    fill_stats(R, k, st, true);  // the levels completed before the failure
     return rc;
+  }
   fill_stats(R, k, st, true);
   const unsigned long long cnt = level < (int)R.levels.size() ? R.levels[level].count : 0ull;
   if ((rc = put(c, count, &cnt, sizeof(cnt)))) return rc;
@@ -790,13 +1199,20 @@ int level_keys_graph(tw_ctx* c, const HostGraph& g, int k, int level, uint64_t* 
     const size_t w = key_bytes(kc);
     const char* src = lr.hkeys ? lr.hkeys : static_cast<const char*>(c->keys.ptr) + lr.off * w;
     if (kc == kKey32) {
-      // 32-bit states widen to the ABI's 64-bit words (the table is free now)
-      if ((rc = grow(c, &c->table, (size_t)cnt * 8, 0))) return rc;
-      TW_LAUNCH(c, launch_widen32(reinterpret_cast<const uint32_t*>(src), static_cast<unsigned long long*>(c->table.ptr),
-                                  cnt, c->stream));
-      src = static_cast<const char*>(c->table.ptr);
+      // 32-bit states widen to the ABI's 64-bit words: by a kernel into a
+      // device buffer of the caller, or on the host side of the copy
+      if (is_device_ptr(keys)) {
+        TW_LAUNCH(c, launch_widen32(reinterpret_cast<const uint32_t*>(src), reinterpret_cast<unsigned long long*>(keys),
+                                    cnt, c->stream));
+      } else {
+        std::vector<uint32_t> narrow((size_t)cnt);
+        TW_CK(cudaMemcpyAsync(narrow.data(), src, (size_t)cnt * 4, cudaMemcpyDefault, c->stream));
+        TW_CK(cudaStreamSynchronize(c->stream));
+        for (unsigned long long x = 0; x < cnt; ++x) keys[x] = narrow[x];
+      }
+    } else if ((rc = put_from_device(c, keys, src, (size_t)cnt * (size_t)g.words * 8))) {
+      return rc;
     }
-    if ((rc = put_from_device(c, keys, src, (size_t)cnt * (size_t)g.words * 8))) return rc;
   }
   TW_CK(cudaStreamSynchronize(c->stream));
   if (st) {
@@ -846,10 +1262,22 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
   int tw = -1;
   DecideResult R;
   int k0 = std::max(lb, k_first);
+  bool fused_done = false;
   if (c->cfg.ub_shortcut && lb == ub && !want_walk) {
     tw = ub;
   } else {
-    for (int k = k0; k < g.n; ++k) {
+    if (fused_eligible(c, g)) {
+      int status = 0, ans = -1, bail_k = -1;
+      rc = run_fused(c, g, kc, k0, g.n - 1, &R, &status, &ans, &bail_k, st);
+      if (rc) return rc;
+      if (status == 1) {
+        tw = ans;
+        fused_done = true;
+      } else if (status == 2) {
+        k0 = bail_k;
+      }
+    }
+    for (int k = k0; k < g.n && !fused_done; ++k) {
       rc = decide_with_options(c, g, kc, k, want_walk, &R);
       if (rc) return rc;
       fill_stats(R, k, st, false);
@@ -862,11 +1290,11 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
   if (tw < 0) return TW_ERR_CUDA;
   if (want_walk && R.yes) {
     SmallLayout L;
-    rc = reconstruct(c, kc, g.n, R);
-    if (rc) return rc;
+    // (the fused solve has already walked back and built the decomposition)
+    if (!fused_done && (rc = reconstruct(c, kc, g.n, R))) return rc;
     int32_t* d_order = reinterpret_cast<int32_t*>(small_at(c, L.order));
     if (c->cfg.disjoint_paths && (rc = upload_graph(c, g, kc))) return rc;  // bags of G itself
-    if (td_parent || td_bags) {
+    if (!fused_done && (td_parent || td_bags)) {
       TW_LAUNCH(c, launch_td(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), g.n, g.words, d_order,
                       reinterpret_cast<int32_t*>(small_at(c, L.parent)),
                       reinterpret_cast<unsigned long long*>(small_at(c, L.bags)), c->stream));

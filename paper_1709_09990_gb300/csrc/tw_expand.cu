@@ -41,14 +41,28 @@ using core::ExpandParams;
 using core::ResidentWarps;
 using core::kFull;
 
-template <class K, int kWarps, int U, bool kMMW = false>
+template <class K, int kWarps, int U, bool kMMW = false, bool kRanged = false>
 __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
     expand_insert_kernel(const ExpandParams<K> p) {
   constexpr int kBits = KeyTraits<K>::kBits;
   __shared__ K sAdj[kBits];
   __shared__ K sState[kWarps * 32];
   __shared__ uint16_t sQueue[kWarps * 32 * kBits];
-  core::expand_level<K, kWarps, U, kMMW>(p, sAdj, sState, sQueue);
+  core::expand_level<K, kWarps, U, kMMW, kRanged>(p, sAdj, sState, sQueue);
+}
+
+// A ranged launch (one hash range of a level whose table is built slice by
+// slice): 4 warps per block, one block per SM slot.
+template <class K, int U>
+cudaError_t launch_ranged(const ExpandParams<K>& p, unsigned long long blocks_needed, cudaStream_t s) {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_insert_kernel<K, 4, U, false, true>, 128, 0);
+  unsigned long long grid = (unsigned long long)sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > blocks_needed) grid = blocks_needed;
+  expand_insert_kernel<K, 4, U, false, true><<<(int)grid, 128, 0, s>>>(p);
+  return cudaGetLastError();
 }
 
 template <class K, int kWarps, int U>
@@ -98,9 +112,16 @@ cudaError_t launch_expand_t(const ExpandLaunch& a, cudaStream_t s) {
   p.ctr = a.ctr;
   p.allowed = core::kfrom_words<K>(a.allowed[0], a.allowed[1]);
   p.mmw = a.mmw;
+  p.ranges = a.ranges > 0 ? a.ranges : 1;
+  p.range = a.range;
   if (a.n_in == 0) return cudaSuccess;
   const unsigned long long chunks = (a.n_in + 31ull) / 32ull;
   const unsigned long long blocks_needed = (chunks + kWarps - 1) / kWarps;
+  if (a.ranges > 0) {
+    const unsigned long long need4 = (chunks + 3) / 4;
+    if (a.table_slots * sizeof(K) > core::kDeepTableBytes) return launch_ranged<K, 2 * TW_INSERT_UNROLL>(p, need4, s);
+    return launch_ranged<K, TW_INSERT_UNROLL>(p, need4, s);
+  }
   if (a.mmw) {
     // minor-min-width pruning (opt-in): its own instantiation, 4 warps
     int per_sm = 0, dev = 0, sms = 0;
@@ -137,7 +158,7 @@ cudaError_t launch_expand_k<K128>(const ExpandLaunch& a, cudaStream_t s) {
 
 // ---------------------------------------------------------------- clearing
 __global__ void clear_kernel(uint4* __restrict__ t, size_t n16, LevelCounters* ctr) {
-  if (blockIdx.x == 0 && threadIdx.x < sizeof(LevelCounters) / sizeof(unsigned long long))
+  if (ctr && blockIdx.x == 0 && threadIdx.x < sizeof(LevelCounters) / sizeof(unsigned long long))
     reinterpret_cast<unsigned long long*>(ctr)[threadIdx.x] = 0ull;
   const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -206,47 +227,7 @@ __global__ void td_kernel(const unsigned long long* __restrict__ adj64, int n, i
                           const int32_t* __restrict__ order, int32_t* parent, unsigned long long* bags) {
   __shared__ K128 sAdj[128];
   __shared__ int sPos[128];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    sAdj[i] = K128{adj64[(size_t)i * words64], words64 > 1 ? adj64[(size_t)i * words64 + 1] : 0ull};
-    sPos[i] = n;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int o = order[i];
-    if (o >= 0 && o < n) sPos[o] = i;  // a malformed order never indexes out of range
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v < n; v += blockDim.x) {
-    const int pv = sPos[v];
-    K128 prefix = kzero<K128>();
-    for (int u = 0; u < n; ++u)
-      if (sPos[u] < pv) prefix |= kbit<K128>(u);
-    K128 q = sAdj[v] & ~prefix;
-    K128 vis = sAdj[v] & prefix;
-    K128 front = vis;
-    while (!kempty(front)) {
-      const int u = klowest(front);
-      front = kdrop_lowest(front);
-      const K128 r = sAdj[u];
-      q |= r & ~prefix;
-      const K128 nw = r & prefix & ~vis;
-      vis |= nw;
-      front |= nw;
-    }
-    q &= ~kbit<K128>(v);
-    const K128 bag = q | kbit<K128>(v);
-    bags[(size_t)v * words64] = bag.lo;
-    if (words64 > 1) bags[(size_t)v * words64 + 1] = bag.hi;
-    int best = -1;
-    K128 t = q;
-    while (!kempty(t)) {
-      const int u = klowest(t);
-      t = kdrop_lowest(t);
-      if (best < 0 || sPos[u] < sPos[best]) best = u;
-    }
-    if (best < 0) best = (pv >= n - 1) ? -1 : order[n - 1];
-    parent[v] = best;
-  }
+  core::td_block(adj64, n, words64, order, parent, bags, sAdj, sPos);
 }
 
 int sm_count() {

@@ -327,6 +327,21 @@ __device__ __forceinline__ K mmw_filter(const K S, K feas, const K* __restrict__
   return feas;
 }
 
+// Keeps the feasible extensions v of S whose new set S u {v} hashes into
+// range `range` of `ranges` equal ranges of the hash space (the same split as
+// the home slot: the high word of hash * ranges).
+template <class K>
+__device__ __forceinline__ K in_hash_range(const K S, K feas, const unsigned long long ranges,
+                                           const unsigned long long range) {
+  K keep = kzero<K>();
+  while (!kempty(feas)) {
+    const K vb = klsb(feas);
+    feas ^= vb;
+    if (__umul64hi(khash(S | vb), ranges) == range) keep |= vb;
+  }
+  return keep;
+}
+
 // Packs the feasible (S, v) pairs of the warp's 32 states into the warp's
 // queue (entry = lane << 8 | v) and stores each lane's S; returns the number
 // of pairs (warp uniform).
@@ -371,11 +386,15 @@ struct LevelOut {
 // inspected, so each lane has several compare-and-swaps in flight.  Linear
 // probing from the home slot, at most max_probes slots.  Winners append
 // (S u {v}, pred or parent) with one atomic add per round of the warp.
-template <class K, bool kParent, int U = TW_INSERT_UNROLL>
+//
+// With kRanged the table is the slice of one hash range (in_hash_range): the
+// home slot spreads the range's hashes over the slice (the high word of
+// (hash * ranges mod 2^64) * slots), and no predecessor is stored.
+template <class K, bool kParent, int U = TW_INSERT_UNROLL, bool kRanged = false>
 __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, const K* __restrict__ sS,
                                              const int total, const int lane, K* __restrict__ table,
                                              const unsigned long long slots, const int max_probes,
-                                             const LevelOut<K, kParent>& out) {
+                                             const LevelOut<K, kParent>& out, const unsigned long long ranges = 1) {
   const K empty = kones<K>();
   const unsigned lanemask_lt = (1u << lane) - 1u;
   for (int base = 0; base < total; base += 32 * U) {
@@ -397,7 +416,7 @@ __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, co
         vv[u] = e & 0xff;
         src[u] = e >> 8;
         key[u] = sS[src[u]] | kbit<K>(vv[u]);
-        h[u] = home_slot(khash(key[u]), slots);
+        h[u] = kRanged ? home_slot(khash(key[u]) * ranges, slots) : home_slot(khash(key[u]), slots);
         st[u] = 1;
       }
     }
@@ -451,7 +470,7 @@ __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, co
             kstore_cs(&out.keys[o], key[u]);
             if (kParent)
               __stcs(&out.parent[o], out.parent_base + (uint32_t)src[u]);
-            else
+            else if (!kRanged)
               __stcs(reinterpret_cast<signed char*>(&out.pred[o]), (signed char)vv[u]);
           } else {
             atomicOr(out.overflow, 1u);
@@ -494,6 +513,8 @@ struct ExpandParams {
   LevelCounters* ctr;
   K allowed;  // vertices that may be added (all by default)
   int mmw;    // 1: minor-min-width pruning of the states before they are extended
+  unsigned long long ranges;  // ranged kernels: the hash space is split in this many ranges,
+  unsigned long long range;   // and only pairs of this one are inserted (the table is its slice)
 };
 
 // One level i -> i+1 by the whole block: the adjacency rows go to shared
@@ -501,7 +522,13 @@ struct ExpandParams {
 // loads), finds their feasible extensions (thread per state), queues the
 // pairs and inserts them cooperatively.  sState holds kWarps x 32 keys,
 // sQueue kWarps x 32 x kBits entries.
-template <class K, int kWarps, int U = TW_INSERT_UNROLL, bool kMMW = false>
+//
+// With kBlockLocal the block expands the whole level alone (its warps take the
+// chunks in turn): a persistent kernel whose blocks work on different graphs.
+// With kKeysL2 the input keys are read through L2 only: persistent kernels,
+// whose arena other SMs rewrite while stale lines may sit in this SM's L1.
+template <class K, int kWarps, int U = TW_INSERT_UNROLL, bool kMMW = false, bool kRanged = false,
+          bool kBlockLocal = false, bool kKeysL2 = false>
 __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, K* sState, uint16_t* sQueue) {
   constexpr int kBits = KeyTraits<K>::kBits;
   for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
@@ -513,7 +540,8 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   const K valid = kfirst_n<K>(p.n);
   unsigned long long generated_total = 0;
   const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
-  const unsigned long long stride = (unsigned long long)gridDim.x * kWarps;
+  const unsigned long long first = kBlockLocal ? (unsigned long long)warp : (unsigned long long)blockIdx.x * kWarps + warp;
+  const unsigned long long stride = kBlockLocal ? (unsigned long long)kWarps : (unsigned long long)gridDim.x * kWarps;
   LevelOut<K, false> out;
   out.keys = p.out_keys;
   out.pred = p.out_pred;
@@ -522,21 +550,106 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   out.cap = p.out_cap;
   out.count = &p.ctr->out_count;
   out.overflow = &p.ctr->overflow;
-  for (unsigned long long chunk = (unsigned long long)blockIdx.x * kWarps + warp; chunk < n_chunks;
-       chunk += stride) {
+  for (unsigned long long chunk = first; chunk < n_chunks; chunk += stride) {
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;
-    const K S = active ? kload_cs(&p.in_keys[idx]) : valid;
+    const K S = active ? (kKeysL2 ? kload_cg(&p.in_keys[idx]) : kload_cs(&p.in_keys[idx])) : valid;
     // (minor-min-width pruning drops some parents, so it extends by every
     // feasible vertex)
     K feas = active ? feasible_extensions<K, !kMMW>(S, sAdj, valid, p.allowed, p.k) : kzero<K>();
     if (kMMW) feas = mmw_filter<K>(S, feas, sAdj, p.n, p.k, lane);
+    if (kRanged) feas = in_hash_range<K>(S, feas, p.ranges, p.range);
     const int total = build_queue<K>(S, feas, lane, sS, sQ);
     generated_total += (unsigned long long)total;
-    insert_queue<K, false, U>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out);
+    insert_queue<K, false, U, kRanged>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out, p.ranges);
     __syncwarp();
   }
   if (lane == 0 && generated_total) atomicAdd(&p.ctr->generated, generated_total);
+}
+
+// The backward walk by one block: from the first set of level `last`, find
+// the current set in level j (keys [level_off[j], + level_cnt[j])), take its
+// predecessor vertex as order[j-1] and drop it, down to level 1; then the
+// vertices outside the final set in increasing order.  sWalk, sFound: shared.
+template <class K>
+__device__ __forceinline__ void walk_block(const K* __restrict__ keys, const uint8_t* __restrict__ pred,
+                                          const unsigned long long* level_off, const unsigned long long* level_cnt,
+                                          int last, int n, int32_t* order, K* sWalk, int* sFound) {
+  if (threadIdx.x == 0) *sWalk = kload_cg(&keys[__ldcg(&level_off[last])]);
+  __syncthreads();
+  const K fin = *sWalk;
+  for (int j = last; j >= 1; --j) {
+    if (threadIdx.x == 0) *sFound = 0;
+    __syncthreads();
+    const K target = *sWalk;
+    __syncthreads();  // every thread has the target before the finder replaces it
+    const unsigned long long lo = __ldcg(&level_off[j]), cnt = __ldcg(&level_cnt[j]);
+    for (unsigned long long x = threadIdx.x; x < cnt; x += blockDim.x) {
+      if (kload_cg(&keys[lo + x]) == target && atomicExch(sFound, 1) == 0) {
+        const int v = __ldcg(&pred[lo + x]);
+        order[j - 1] = v;
+        *sWalk = target & ~kbit<K>(v);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int pos = last;
+    for (int v = 0; v < n; ++v)
+      if (!ktest(fin, v)) order[pos++] = v;
+  }
+  __syncthreads();
+}
+
+// Tree decomposition from an ordering, by one block (thread per vertex):
+// bag(v) = {v} u Q(prefix(v), v) and parent(v) = the vertex of Q(prefix(v), v)
+// eliminated first after v (the last vertex of the order when Q is empty; the
+// last vertex is the root, -1).  adj64 / bags: n rows x words64 uint64;
+// sAdj, sPos: shared arrays of 128 entries.
+__device__ __forceinline__ void td_block(const unsigned long long* __restrict__ adj64, int n, int words64,
+                                         const int32_t* __restrict__ order, int32_t* parent,
+                                         unsigned long long* bags, K128* sAdj, int* sPos) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sAdj[i] = K128{adj64[(size_t)i * words64], words64 > 1 ? adj64[(size_t)i * words64 + 1] : 0ull};
+    sPos[i] = n;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int o = order[i];
+    if (o >= 0 && o < n) sPos[o] = i;  // a malformed order never indexes out of range
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    const int pv = sPos[v];
+    K128 prefix = kzero<K128>();
+    for (int u = 0; u < n; ++u)
+      if (sPos[u] < pv) prefix |= kbit<K128>(u);
+    K128 q = sAdj[v] & ~prefix;
+    K128 vis = sAdj[v] & prefix;
+    K128 front = vis;
+    while (!kempty(front)) {
+      const int u = klowest(front);
+      front = kdrop_lowest(front);
+      const K128 r = sAdj[u];
+      q |= r & ~prefix;
+      const K128 nw = r & prefix & ~vis;
+      vis |= nw;
+      front |= nw;
+    }
+    q &= ~kbit<K128>(v);
+    const K128 bag = q | kbit<K128>(v);
+    bags[(size_t)v * words64] = bag.lo;
+    if (words64 > 1) bags[(size_t)v * words64 + 1] = bag.hi;
+    int best = -1;
+    K128 t = q;
+    while (!kempty(t)) {
+      const int u = klowest(t);
+      t = kdrop_lowest(t);
+      if (best < 0 || sPos[u] < sPos[best]) best = u;
+    }
+    if (best < 0) best = (pv >= n - 1) ? -1 : order[n - 1];
+    parent[v] = best;
+  }
 }
 
 }  // namespace core

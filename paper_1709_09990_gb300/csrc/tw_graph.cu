@@ -147,6 +147,8 @@ cudaError_t expand_t(const GraphState* st, const ExpandLaunch& a, cudaStream_t s
   p.ctr = a.ctr;
   p.allowed = core::kfrom_words<K>(a.allowed[0], a.allowed[1]);
   p.mmw = a.mmw;
+  p.ranges = 1;
+  p.range = 0;
   int per_sm = 0;
   if (a.mmw) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, graph_expand_kernel<K, kWarps, true>, kWarps * 32, 0);

@@ -53,7 +53,7 @@ int put_from_device(tw_ctx* c, void* dst, const void* src_dev, size_t bytes) {
 }
 
 size_t total_bytes(const tw_ctx* c) {
-  return c->keys.bytes + c->pred.bytes + c->table.bytes + c->cand_key.bytes + c->cand_v.bytes;
+  return c->keys.bytes + c->pred.bytes + c->table.bytes + c->cand_key.bytes + c->cand_v.bytes + c->ooc_keys.bytes;
 }
 
 // Takes bytes (rounded up to 256) of pinned, device-mapped host memory from

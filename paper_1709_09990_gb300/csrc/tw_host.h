@@ -45,6 +45,7 @@ struct DevBuf {
 }  // namespace host
 }  // namespace tw
 
+using tw::FusedState;
 using tw::GraphState;
 using tw::LevelCounters;
 using tw::host::DevBuf;
@@ -58,6 +59,7 @@ struct tw_ctx {
   DevBuf keys, pred, table, small;  // small: adjacency, walk, order, td scratch
   DevBuf scratch;                    // staged batch inputs/outputs and network data
   DevBuf cand_key, cand_v, part_meta;  // regions of the partitioned insert
+  DevBuf ooc_keys;                   // second level buffer of out-of-core decide runs
   LevelCounters* d_ctr = nullptr;
   LevelCounters* h_ctr = nullptr;
   int sms = 0;
@@ -90,6 +92,14 @@ struct tw_ctx {
   };
   std::vector<HostChunk> host_chunks;
   size_t host_chunk = 0, host_used = 0;  // allocation cursor of the current run
+  // out-of-core decide runs: two pinned, device-mapped host buffers that hold
+  // the levels that do not fit the device (reused from run to run)
+  HostChunk ooc_host[2] = {{nullptr, nullptr, 0}, {nullptr, nullptr, 0}};
+  // fused small solves: state, two tables and the level arena in one buffer,
+  // a pinned mirror of the state, and the graphs whose fused run gave up
+  DevBuf fused;
+  FusedState* h_fused = nullptr;
+  std::vector<unsigned long long> fused_skip;
   // options of Section 3.1 for the decide run being prepared
   unsigned long long allowed[2] = {~0ull, ~0ull};
   int skipped = 0;  // vertices excluded from the sets (|C| with the clique skip)

@@ -44,11 +44,15 @@ struct ExpandLaunch {
   int grid;                      // 0 = derived from the occupancy of this device
   unsigned long long allowed[2]; // vertices that may be added (low word first)
   int mmw;                       // 1: minor-min-width pruning (Section 3.3)
+  unsigned long long ranges = 0; // > 0: ranged launch - only the pairs whose hash lies in
+  unsigned long long range = 0;  // range `range` of `ranges` are inserted, into a table that
+                                 // is that range's slice; out_pred is not written
 };
 
 cudaError_t launch_expand(const ExpandLaunch& a, cudaStream_t s);
 
-// Sets every slot of a table to the empty key (all ones) and zeroes ctr.
+// Sets every slot of a table to the empty key (all ones) and zeroes ctr
+// (unless ctr is null).
 cudaError_t launch_clear(void* table, size_t table_bytes, LevelCounters* ctr, cudaStream_t s);
 
 // dst[i] = src[i] zero-extended, i < count (32-bit states in 64-bit words).
@@ -134,6 +138,76 @@ cudaError_t launch_graph_clear(KeyClass kc, const GraphState* st, void* table, c
 // base: in_keys/out_keys = the arena, out_pred = the predecessor arena; the
 // level fields come from st.
 cudaError_t launch_graph_expand(const GraphState* st, const ExpandLaunch& base, cudaStream_t s);
+
+// ---- fused small solve (tw_fused.cu) -----------------------------------------
+// Device state of a fused solve (zeroed by the host before the launch).
+struct FusedState {
+  unsigned long long level_off[130];  // arena index of level j of the final run
+  unsigned long long level_cnt[130];  // |L_j|
+  LevelCounters ctr[130];             // counters of the expansion that built level j
+  unsigned long long states_expanded, candidates, generated;  // over every decide run
+  unsigned int arrive, gen, error;    // grid barrier; error: a barrier wait gave up
+  int status;                         // 1: finished, 2: gave up at k = last (the host goes on)
+  int tw, last;                       // the first yes k (-1: none up to k_last) and the
+                                      // index of the final level of the last run
+};
+
+struct FusedLaunch {
+  KeyClass kc;                        // kKey32 or kKey64
+  const void* adj;                    // n rows in the state layout
+  const unsigned long long* adj64;    // n rows of words64 words
+  int n, words64, k0, k_last, max_probes, load_pct;  // decide runs at k0 .. k_last
+  void* keys;                         // arena of arena_cap states
+  uint8_t* pred;
+  unsigned long long arena_cap;
+  void* table0;
+  void* table1;
+  unsigned long long table_cap;       // slots of each table
+  FusedState* st;
+  int32_t* order;
+  int32_t* parent;
+  unsigned long long* bags;
+};
+
+// The k sweep from k0, the walk and the tree decomposition of one graph
+// (n <= 64) in one cooperative launch; see tw_fused.cu.
+cudaError_t launch_fused_solve(const FusedLaunch& f, cudaStream_t s);
+
+// ---- persistent batched solve (tw_batch_solve.cu) ----------------------------
+struct BatchSolveArgs {
+  const unsigned long long* adj;      // 64 rows per graph
+  const int32_t* n;
+  const int32_t* lb;                  // lower bound of each graph (certification)
+  const int32_t* k_start;             // first k of each graph (decide mode: its k)
+  int num_graphs;
+  int decide_mode;                    // 1: one decide per graph, level sizes and fingerprints
+  int max_probes, load_pct;
+  unsigned int* next_graph;           // the work queue (zero before the launch)
+  // workspace of each block (blockIdx.x): A keys + A predecessor bytes, two
+  // tables of T slots, counters, level offsets and sizes (130 each)
+  unsigned long long* arena;
+  uint8_t* pred;
+  unsigned long long* tables;
+  LevelCounters* ctr;
+  unsigned long long* level_off;
+  unsigned long long* level_cnt;
+  unsigned long long A, T;
+  // results
+  int32_t* tw;                        // solve mode (-1 when the graph was left to the host)
+  int32_t* orders;                    // solve mode, or null
+  const int64_t* order_off;
+  int32_t* status;                    // 0 done, 2 outgrew the workspace
+  int32_t* yes;                       // decide mode
+  int32_t* last;                      // decide mode: index of the final level
+  unsigned long long* level_size;     // decide mode: 129 per graph
+  unsigned long long* fp_sum;         // decide mode (or null): 129 per graph
+  unsigned long long* fp_xor;
+  unsigned long long* totals;         // states expanded, candidates, generated pairs, decide runs
+};
+
+// Resident blocks of the kernel with `warps` warps per block (4 or 8).
+int batch_solve_blocks(int warps);
+cudaError_t launch_batch_solve(const BatchSolveArgs& a, int blocks, int warps, cudaStream_t s);
 
 // ---- batched expansion (tw_batch.cu) ---------------------------------------
 // One graph's share of a batched level step (64-bit states, n <= 64).

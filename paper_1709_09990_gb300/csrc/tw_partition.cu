@@ -270,6 +270,8 @@ cudaError_t emit_t(const ExpandLaunch& a, const PartitionBufs& pb, cudaStream_t 
   p.ctr = a.ctr;
   p.allowed = core::kfrom_words<K>(a.allowed[0], a.allowed[1]);
   p.mmw = a.mmw;
+  p.ranges = 1;
+  p.range = 0;
   const unsigned long long blocks_needed = (a.n_in + kWarps * 32 - 1) / (kWarps * 32);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_kernel<K>, kWarps * 32, 0);

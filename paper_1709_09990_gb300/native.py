@@ -36,7 +36,9 @@ class Config(ctypes.Structure):
                 ("max_probes", ctypes.c_int), ("ub_shortcut", ctypes.c_int), ("graph_levels", ctypes.c_int),
                 ("time_kernels", ctypes.c_int), ("clique_skip", ctypes.c_int), ("disjoint_paths", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("partition_table_mb", ctypes.c_int), ("mmw_prune", ctypes.c_int),
-                ("spill_levels", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("spill_levels", ctypes.c_int), ("out_of_core", ctypes.c_int),
+                ("fused_states", ctypes.c_int), ("batch_kernel", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -142,7 +144,8 @@ class Context:
                  stream: int = 0, block_threads: int = 0, table_load_pct: int = 0, max_probes: int = 0,
                  ub_shortcut: bool = False, time_kernels: bool = False, graph_levels: int = 0,
                  autotune: bool = False, clique_skip: bool = False, disjoint_paths: bool = False,
-                 partition_table_mb: int = 0, mmw_prune: bool = False, spill_levels: bool = False):
+                 partition_table_mb: int = 0, mmw_prune: bool = False, spill_levels: bool = False,
+                 out_of_core: bool = False, fused_states: int = 0, batch_kernel: int = 0):
         cfg = Config()
         cfg.device = device
         cfg.fingerprints = int(fingerprints)
@@ -160,6 +163,9 @@ class Context:
         cfg.partition_table_mb = int(partition_table_mb)
         cfg.mmw_prune = int(mmw_prune)
         cfg.spill_levels = int(spill_levels)
+        cfg.out_of_core = int(out_of_core)
+        cfg.fused_states = int(fused_states)
+        cfg.batch_kernel = int(batch_kernel)
         h = _vp()
         _check(lib().tw_create(ctypes.byref(h), ctypes.byref(cfg)), "tw_create")
         self._h = h
@@ -197,11 +203,13 @@ class Context:
                 raise err
         return {"status": rc, "yes": bool(yes.value == 1), "order": order, "stats": st.as_dict()}
 
-    def decide_level(self, adj, k: int, level: int, n: Optional[int] = None, keys_out=None):
+    def decide_level(self, adj, k: int, level: int, n: Optional[int] = None, keys_out=None,
+                     count_only: bool = False):
         """The sets of level ``level`` of decide(k) as a (count, ceil(n/64))
         uint64 array (unordered).  keys_out (host array or device tensor of
         at least count * ceil(n/64) words) is used when given; otherwise a host
-        array is sized from a first call that returns the count only."""
+        array is sized from a first call that returns the count only.  With
+        count_only no sets are copied (keys is None)."""
         rows = rows_u64(adj)
         n = len(adj) if n is None else n
         w = max(1, (n + 63) // 64)
@@ -210,8 +218,10 @@ class Context:
         if keys_out is None:
             rc = lib().tw_decide_level(self._h, _ptr(rows), n, k, level, None, 0, ctypes.byref(cnt),
                                        ctypes.byref(st))
-            if rc not in (TW_OK, TW_ERR_CAPACITY):
+            if rc not in (TW_OK, TW_ERR_CAPACITY) or (rc == TW_ERR_CAPACITY and cnt.value == 0):
                 _check(rc, "tw_decide_level")
+            if count_only:
+                return {"keys": None, "count": int(cnt.value), "stats": st.as_dict()}
             keys_out = np.zeros((max(1, int(cnt.value)), w), np.uint64)
         cap = (keys_out.numel() if hasattr(keys_out, "numel") else keys_out.size) // w
         rc = lib().tw_decide_level(self._h, _ptr(rows), n, k, level, _ptr(keys_out), cap, ctypes.byref(cnt),

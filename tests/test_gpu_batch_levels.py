@@ -31,9 +31,10 @@ def _rows(res, g):
     return sizes[: last + 1], res["fp_sum"][g][: last + 1].tolist(), res["fp_xor"][g][: last + 1].tolist()
 
 
-def test_batch_levels_match_oracle_and_single_graph_path():
+@pytest.mark.parametrize("batch_kernel", [0, 1], ids=["persistent", "level_synchronous"])
+def test_batch_levels_match_oracle_and_single_graph_path(batch_kernel):
     graphs = [a for a in gg.batch_graphs(400) if len(a) <= 30]
-    with context(fingerprints=True) as ctx:
+    with context(fingerprints=True, batch_kernel=batch_kernel) as ctx:
         sol = ctx.solve_batch(graphs, want_orders=False)
         assert np.all(sol["per_graph_status"] == 0)
         tw = sol["tw"]
@@ -59,13 +60,14 @@ def test_batch_levels_match_oracle_and_single_graph_path():
         assert checked_oracle >= 150
 
 
-def test_batch_levels_edge_cases():
+@pytest.mark.parametrize("batch_kernel", [0, 1], ids=["persistent", "level_synchronous"])
+def test_batch_levels_edge_cases(batch_kernel):
     # n > 64 (the single-graph path inside the batch call: the path P_70 at
     # k = 1, |L_i| = i + 1, and at k = 0, where L_1 is empty), k >= n-1 (the
     # single level {empty set}), an empty first level (K_7 at k = 2), n = 1
     graphs = [gg.path(70), gg.path(70), gg.complete(7), gg.workload_gnp20(), [0], gg.path(9)]
     ks = np.array([1, 0, 2, 25, 0, 1], np.int32)
-    with context(fingerprints=True) as ctx:
+    with context(fingerprints=True, batch_kernel=batch_kernel) as ctx:
         res = ctx.decide_batch(graphs, ks)
         assert res["status"] == 0
         for g, adj in enumerate(graphs):
@@ -81,3 +83,31 @@ def test_batch_levels_edge_cases():
         # a negative bound is refused for that graph only
         bad = ctx.decide_batch(graphs[:3], np.array([-1, 0, 2], np.int32))
         assert bad["per_graph_status"].tolist() == [1, 0, 0]
+
+
+def test_persistent_batch_equals_level_synchronous_and_loop():
+    # the same answers and verified orderings from the persistent kernel, the
+    # level-synchronous kernel and a per-graph tw_solve loop, with proposed
+    # bounds above, at and below tw
+    graphs = [gg.mixed_graph(5000 + j, 12, 34, j % 2 == 0) for j in range(96)]
+    with context() as ctx, context(batch_kernel=1) as sync:
+        loop = [ctx.solve(a, want_order=False)["tw"] for a in graphs]
+        for hint in (None, np.array(loop, np.float32) + 2, np.array(loop, np.float32) - 1):
+            a = ctx.solve_batch(graphs, k_hint=hint)
+            b = sync.solve_batch(graphs, k_hint=hint)
+            assert a["status"] == 0 and b["status"] == 0
+            assert a["tw"].tolist() == b["tw"].tolist() == loop
+            pos = 0
+            for g, adj in enumerate(graphs):
+                order = a["orders"][pos: pos + len(adj)].tolist()
+                assert sorted(order) == list(range(len(adj)))
+                assert oracle.width_elim(adj, order) == loop[g]
+                pos += len(adj)
+    # graphs whose levels stay small never leave the persistent kernel: the
+    # bounds and one launch for the whole batch
+    small = [gg.mixed_graph(6000 + j, 10, 20, j % 2 == 0) for j in range(200)]
+    with context() as ctx, context(batch_kernel=1) as sync:
+        a = ctx.solve_batch(small)
+        b = sync.solve_batch(small)
+    assert a["tw"].tolist() == b["tw"].tolist()
+    assert a["stats"]["kernel_launches"] == 2 < b["stats"]["kernel_launches"]
