@@ -89,12 +89,14 @@ typedef struct {
                              (state width, n/8) and reuse the choice; the level
                              is recomputed per candidate, results are unchanged.
                              Explicit block_threads / table_load_pct win.        */
-  int partition_table_mb; /* > 0: levels whose hash table exceeds this many MB
-                             insert in two launches, by hash range, so that the
-                             part of the table being filled stays in L2; -2:
-                             every level; 0 or -1: never (default: measured
-                             slower than the direct insert on GB300 for the
-                             levels tried).  Results are unchanged.             */
+  int partition_table_mb; /* levels whose hash table exceeds this many MB insert
+                             in two steps: the search writes the pairs grouped
+                             by hash range, then the ranges are inserted one by
+                             one into their slice of the table, which is emptied
+                             in L2 just before and dropped from L2 without a
+                             write-back after, so the table stays out of DRAM.
+                             0 = 256 MB (the default), -1 = never, -2 = every
+                             level.  Results are unchanged.                     */
   int mmw_prune;          /* 1 = Section 3.3: a state whose remaining graph has a
                              minor-min-width bound (second-smallest degree of each
                              contraction step) above k is not extended.  Answers

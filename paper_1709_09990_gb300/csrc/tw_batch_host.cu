@@ -207,7 +207,7 @@ int run_batch(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector
     if ((rc = dev_alloc(&d_n, G)) || (rc = dev_alloc(&d_off, G)) || (rc = dev_alloc(&d_b, (size_t)G * 4))) return rc;
     TW_CK(cudaMemcpyAsync(d_n, ns.data(), G * 4, cudaMemcpyHostToDevice, c->stream));
     TW_CK(cudaMemcpyAsync(d_off, offs.data(), G * 8, cudaMemcpyHostToDevice, c->stream));
-    TW_LAUNCH(c, launch_bounds(B.adj, d_n, d_off, G, d_b, nullptr, c->stream));
+    TW_LAUNCH(c, launch_bounds(B.adj, d_n, d_off, G, d_b, nullptr, c->stream, 1));
     std::vector<int32_t> b((size_t)G * 4);
     TW_CK(cudaMemcpyAsync(b.data(), d_b, b.size() * 4, cudaMemcpyDeviceToHost, c->stream));
     TW_CK(cudaStreamSynchronize(c->stream));
@@ -559,7 +559,7 @@ int run_batch_persistent(tw_ctx* c, const std::vector<HostGraph>& graphs, const 
   TW_CK(cudaMemcpyAsync(d_n, ns.data(), (size_t)G * 4, cudaMemcpyHostToDevice, c->stream));
   TW_CK(cudaMemcpyAsync(d_off, offs.data(), (size_t)G * 8, cudaMemcpyHostToDevice, c->stream));
   TW_CK(cudaMemcpyAsync(d_ooff, ooff.data(), (size_t)G * 8, cudaMemcpyHostToDevice, c->stream));
-  TW_LAUNCH(c, launch_bounds(d_adj, d_n, d_off, G, d_b, nullptr, c->stream));
+  TW_LAUNCH(c, launch_bounds(d_adj, d_n, d_off, G, d_b, nullptr, c->stream, 1));
   std::vector<int32_t> b((size_t)G * 4);
   TW_CK(cudaMemcpyAsync(b.data(), d_b, b.size() * 4, cudaMemcpyDeviceToHost, c->stream));
   TW_CK(cudaStreamSynchronize(c->stream));

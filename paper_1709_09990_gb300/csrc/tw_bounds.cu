@@ -153,7 +153,7 @@ __device__ int ub_min_fill(K128* rows, const unsigned long long* adj, int n, int
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     bounds_kernel(const unsigned long long* __restrict__ adj, const int32_t* __restrict__ ns,
-                  const int64_t* __restrict__ offs, int num_graphs, int32_t* out, float* feats) {
+                  const int64_t* __restrict__ offs, int num_graphs, int32_t* out, float* feats, int lower_only) {
   __shared__ K128 sRows[kWarpsPerBlock][128];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -165,8 +165,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   K128* rows = sRows[warp];
   const int mmd = bound_mmd(rows, a, n, W, lane);
   const int mmdp = bound_mmd_plus(rows, a, n, W, lane);
-  const int ubd = ub_min_degree(rows, a, n, W, lane);
-  const int ubf = ub_min_fill(rows, a, n, W, lane);
+  // (the greedy widths take most of the time; a k sweep needs only the lower bounds)
+  const bool ub = !lower_only || feats;
+  const int ubd = ub ? ub_min_degree(rows, a, n, W, lane) : -1;
+  const int ubf = ub ? ub_min_fill(rows, a, n, W, lane) : -1;
   if (out && lane == 0) {
     out[4 * g + 0] = mmd;
     out[4 * g + 1] = mmdp;
@@ -225,10 +227,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }  // namespace
 
 cudaError_t launch_bounds(const unsigned long long* adj, const int32_t* n, const int64_t* row_offset, int num_graphs,
-                          int32_t* out, float* feats, cudaStream_t s) {
+                          int32_t* out, float* feats, cudaStream_t s, int lower_only) {
   if (num_graphs <= 0) return cudaSuccess;
   const int blocks = (num_graphs + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  bounds_kernel<<<blocks, kWarpsPerBlock * 32, 0, s>>>(adj, n, row_offset, num_graphs, out, feats);
+  bounds_kernel<<<blocks, kWarpsPerBlock * 32, 0, s>>>(adj, n, row_offset, num_graphs, out, feats, lower_only);
   return cudaGetLastError();
 }
 

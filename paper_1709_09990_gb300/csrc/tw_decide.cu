@@ -26,18 +26,24 @@
 namespace tw {
 namespace host {
 
-// Table size above which a level takes the partitioned insert (opt-in: on
-// the heavy levels measured on GB300 the direct kernel, which overlaps its
-// DRAM compare-and-swaps with the search, was 30-40% faster).
+// Table size above which a level takes the partitioned insert: by default
+// tables of more than 256 MB (about twice the L2), where the direct kernel's
+// compare-and-swaps go to DRAM.
 unsigned long long partition_threshold_bytes(const tw_ctx* c) {
   if (c->cfg.partition_table_mb == -2) return 0ull;
-  if (c->cfg.partition_table_mb <= 0) return ~0ull;
+  if (c->cfg.partition_table_mb < 0) return ~0ull;
+  if (c->cfg.partition_table_mb == 0) return 256ull << 20;
   return (unsigned long long)c->cfg.partition_table_mb << 20;
 }
 
 // One level through the partitioned insert (emit, then insert range by
-// range), on a cleared table.  *fallback is set when a region overflowed
-// (the caller then runs the direct kernel on a freshly cleared table).
+// range); the caller has zeroed the counters but not the table.  When the
+// whole level is emitted in one chunk, each range's slice of the table
+// (plus the slots its probes can run into) is emptied just before the
+// range's inserts and dropped from L2 afterwards without a write-back, so
+// the table never travels to DRAM; with several chunks the whole table is
+// emptied first and kept.  *fallback is set when a region overflowed (the
+// caller then runs the direct kernel on a freshly cleared table).
 int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, bool* fallback) {
   *fallback = false;
   const size_t w = key_bytes(a.kc);
@@ -75,6 +81,8 @@ int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, 
   pb.overflow = reinterpret_cast<unsigned int*>(pb.prefix + kMaxRanges + 1);
   std::vector<unsigned long long> cnt(P), prefix(P + 1);
   const size_t kw = key_bytes(a.kc);
+  const bool one_chunk = chunk >= a.n_in;
+  if (!one_chunk) TW_LAUNCH(c, launch_clear(a.table, (size_t)((a.table_slots * kw + 15) & ~15ull), nullptr, c->stream));
   for (unsigned long long lo = 0; lo < a.n_in; lo += chunk) {
     ExpandLaunch ca = a;
     ca.in_keys = static_cast<const char*>(a.in_keys) + lo * kw;
@@ -92,7 +100,21 @@ int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, 
     prefix[0] = 0;
     for (int r = 0; r < P; ++r) prefix[r + 1] = prefix[r] + std::min(cnt[r], region_cap);
     TW_CK(cudaMemcpyAsync(pb.prefix, prefix.data(), (P + 1) * 8, cudaMemcpyHostToDevice, c->stream));
-    TW_LAUNCH(c, launch_insert_ranges(ca, pb, prefix[P], c->stream));
+    if (!one_chunk) {
+      TW_LAUNCH(c, launch_insert_ranges(ca, pb, 0, prefix[P], c->stream));
+      continue;
+    }
+    // range r's home slots are [r S / P, (r+1) S / P); its probes may run up
+    // to max_probes slots further (wrapping at the end of the table)
+    const unsigned long long S = a.table_slots;
+    for (int r = 0; r < P; ++r) {
+      const unsigned long long s_lo = (unsigned long long)(((unsigned __int128)S * r) / P);
+      const unsigned long long s_hi = (unsigned long long)(((unsigned __int128)S * (r + 1)) / P);
+      const unsigned long long span = std::min<unsigned long long>(S, s_hi - s_lo + (unsigned long long)a.max_probes);
+      TW_LAUNCH(c, launch_clear_slots(a.kc, a.table, s_lo, span, S, c->stream));
+      TW_LAUNCH(c, launch_insert_ranges(ca, pb, prefix[r], prefix[r + 1], c->stream));
+      TW_LAUNCH(c, launch_discard_l2(a.table, s_lo * kw, s_hi * kw, c->stream));
+    }
   }
   return TW_OK;
 }
@@ -491,7 +513,12 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       if (rc == TW_OK) rc = grow(c, &c->pred, (size_t)(off + out_cap), (size_t)live_end);
       if (rc == TW_ERR_CAPACITY && ooc) return run_decide_ooc(c, kc, n, k, R, stop_level);
       if (rc) return rc;
-      TW_LAUNCH(c, launch_clear(c->table.ptr, table_bytes, c->d_ctr, c->stream));
+      // (the partitioned insert empties the table itself, range by range)
+      const bool partitioned = (unsigned long long)table_bytes > partition_threshold_bytes(c);
+      if (partitioned)
+        TW_CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(LevelCounters), c->stream));
+      else
+        TW_LAUNCH(c, launch_clear(c->table.ptr, table_bytes, c->d_ctr, c->stream));
       ExpandLaunch a;
       a.kc = kc;
       a.in_keys = static_cast<char*>(c->keys.ptr) + cur.off * w;
@@ -514,7 +541,7 @@ int run_decide(tw_ctx* c, KeyClass kc, int n, int k, bool keep_levels, DecideRes
       const bool timed = c->cfg.time_kernels != 0;
       if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
       bool direct = true;
-      if ((unsigned long long)table_bytes > partition_threshold_bytes(c)) {
+      if (partitioned) {
         bool fallback = false;
         // Regions are sized by the pairs per state of the previous level
         // (with slack), not by the n-i candidates: with canonical parents a
@@ -1222,7 +1249,7 @@ int level_keys_graph(tw_ctx* c, const HostGraph& g, int k, int level, uint64_t* 
   return TW_OK;
 }
 
-int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]) {
+int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4], bool lower_only) {
   SmallLayout L;
   int32_t* d_out = reinterpret_cast<int32_t*>(small_at(c, L.bounds));
   int32_t* d_n = d_out + 4;
@@ -1232,7 +1259,7 @@ int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]) {
   TW_CK(cudaMemcpyAsync(d_n, &nn, 4, cudaMemcpyHostToDevice, c->stream));
   TW_CK(cudaMemcpyAsync(d_off, &off, 8, cudaMemcpyHostToDevice, c->stream));
   TW_LAUNCH(c, launch_bounds(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), d_n, d_off, 1, d_out,
-                      nullptr, c->stream));
+                      nullptr, c->stream, lower_only ? 1 : 0));
   TW_CK(cudaMemcpyAsync(out, d_out, 16, cudaMemcpyDeviceToHost, c->stream));
   TW_CK(cudaStreamSynchronize(c->stream));
   return TW_OK;
@@ -1248,7 +1275,7 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
   int rc = upload_graph(c, g, kc);
   if (rc) return rc;
   int32_t b[4];
-  rc = bounds_graph(c, g, b);
+  rc = bounds_graph(c, g, b, !c->cfg.ub_shortcut);  // the widths only for the shortcut
   if (rc) return rc;
   const int lb = std::max(b[0], b[1]);
   const int ub = std::min(b[2], b[3]);
@@ -1326,7 +1353,7 @@ int solve_hinted(tw_ctx* c, const HostGraph& g, float hint, int* tw_out, std::ve
   int rc = upload_graph(c, g, kc);
   if (rc) return rc;
   int32_t b[4];
-  if ((rc = bounds_graph(c, g, b))) return rc;
+  if ((rc = bounds_graph(c, g, b, true))) return rc;
   const int lb = std::max(b[0], b[1]);
   int k0 = (int)std::lround(hint);
   k0 = std::min(std::max(k0, lb), g.n - 1);

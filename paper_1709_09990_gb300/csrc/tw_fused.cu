@@ -15,8 +15,8 @@
 // The run gives up (status "bail") when a level would not fit the arena or
 // the table, or when a table fills; the host then continues the sweep with
 // its own loop from that k.  Every barrier wait is bounded: a barrier that
-// does not complete within about a second sets an error flag, and all blocks
-// return.
+// does not complete within a second (the global timer) sets an error flag,
+// and all blocks return.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -30,35 +30,59 @@ namespace {
 using core::ExpandParams;
 using core::ResidentWarps;
 constexpr int kFusedWarps = 4;
-constexpr unsigned long long kBarrierSpins = 1ull << 24;  // x 64 ns sleeps: about a second
+constexpr unsigned long long kBarrierNs = 1000000000ull;  // a barrier wait gives up after a second
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(unsigned int* p, unsigned int v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // Bounded grid barrier over all blocks of a cooperative launch (which are
-// co-resident): the last block to arrive resets the count and advances the
-// generation; the others wait for the generation to change, or give up and
-// set *error.  Returns false once any block has given up.
+// co-resident).  The block's threads meet at a block barrier; its thread 0
+// arrives with an acquire-release add (which also publishes the block's
+// writes); the last block to arrive resets the count and advances the
+// generation with a release; the others poll the generation with acquire
+// loads, or give up after kBarrierNs and set st->error.  Returns false once
+// any block has given up.
 __device__ bool grid_barrier(FusedState* st) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = &st->gen;
-    volatile unsigned int* err = &st->error;
-    const unsigned int g = *gen;
-    __threadfence();
-    const unsigned int prev = atomicAdd(&st->arrive, 1u);
+    const unsigned int g = ld_acquire(&st->gen);
+    const unsigned int prev = atom_add_acq_rel(&st->arrive, 1u);
     if (prev == gridDim.x - 1) {
-      st->arrive = 0u;
-      __threadfence();
-      atomicAdd(&st->gen, 1u);
+      st_relaxed(&st->arrive, 0u);
+      red_add_release(&st->gen, 1u);
     } else {
-      unsigned long long spins = 0;
-      while (*gen == g && *err == 0u) {
-        if (++spins > kBarrierSpins) {
-          atomicExch(&st->error, 1u);
-          break;
+      const unsigned long long t0 = global_ns();
+      unsigned int polls = 0;
+      while (ld_acquire(&st->gen) == g) {
+        if ((++polls & 255u) == 0u) {
+          if (ld_acquire(&st->error) != 0u) break;
+          if (global_ns() - t0 > kBarrierNs) {
+            atomicExch(&st->error, 1u);
+            break;
+          }
         }
-        __nanosleep(64);
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return *(volatile unsigned int*)&st->error == 0u;
@@ -243,9 +267,9 @@ cudaError_t launch_t(const FusedLaunch& f, cudaStream_t s) {
   if (!coop) return cudaErrorNotSupported;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_solve_kernel<K>, kFusedWarps * 32, 0);
   if (per_sm < 1) return cudaErrorNotSupported;
-  // two blocks per SM at most: enough warps for levels of a few thousand
-  // states, and a cheap barrier
-  const int grid = sms * (per_sm < 2 ? per_sm : 2);
+  // one block per SM: enough warps for levels of a few thousand states, and
+  // few arrivals per barrier
+  const int grid = sms;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fused_solve_kernel<K>), dim3(grid),
                                      dim3(kFusedWarps * 32), args, 0, s);

@@ -182,7 +182,7 @@ double binom(int n, int r);
 int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order, tw_stats* st);
 int level_keys_graph(tw_ctx* c, const HostGraph& g, int k, int level, uint64_t* keys, uint64_t cap, uint64_t* count,
                      tw_stats* st);
-int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4]);
+int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4], bool lower_only = false);
 int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int32_t* td_parent, uint64_t* td_bags,
                 tw_stats* st, int k_first);
 int solve_hinted(tw_ctx* c, const HostGraph& g, float hint, int* tw_out, std::vector<int32_t>* order_host,

@@ -84,9 +84,10 @@ cudaError_t launch_td(const unsigned long long* adj64, int n, int words64, const
                       int32_t* parent, unsigned long long* bags, cudaStream_t s);
 
 // Bounds (one warp per graph): out[4*g + 0..3] = MMD, MMD+, min-degree width,
-// min-fill width.  Graph g: n[g] rows of ceil(n[g]/64) words at row_offset[g].
+// min-fill width (-1 for the widths with lower_only, unless feats is given).  Graph g: n[g] rows of ceil(n[g]/64) words at row_offset[g].
 cudaError_t launch_bounds(const unsigned long long* adj, const int32_t* n, const int64_t* row_offset,
-                          int num_graphs, int32_t* out, float* feats, cudaStream_t s);
+                          int num_graphs, int32_t* out, float* feats, cudaStream_t s,
+                          int lower_only = 0);
 
 // ---- partitioned insert (tw_partition.cu) ----------------------------------
 constexpr int kMaxRanges = 64;
@@ -106,10 +107,16 @@ struct PartitionBufs {
 // Launch A: search + per-block counting sort of the pairs into the regions
 // (adds the count of generated pairs to a.ctr).
 cudaError_t launch_emit(const ExpandLaunch& a, const PartitionBufs& pb, cudaStream_t s);
-// Launch B: insert the total region entries range after range into a.table,
-// appending winners to a.out_keys / a.out_pred.
-cudaError_t launch_insert_ranges(const ExpandLaunch& a, const PartitionBufs& pb, unsigned long long total,
-                                 cudaStream_t s);
+// Launch B: insert entries [first, end) of the concatenated regions (range-
+// major) into a.table, appending winners to a.out_keys / a.out_pred.
+cudaError_t launch_insert_ranges(const ExpandLaunch& a, const PartitionBufs& pb, unsigned long long first,
+                                 unsigned long long end, cudaStream_t s);
+// Empties slots [first, first + count) of a table of total slots (wrapping).
+cudaError_t launch_clear_slots(KeyClass kc, void* table, unsigned long long first, unsigned long long count,
+                               unsigned long long total, cudaStream_t s);
+// Drops the whole 128-byte lines of bytes [lo, hi) of base from L2 without
+// writing them back (their contents become undefined).
+cudaError_t launch_discard_l2(void* base, unsigned long long lo_bytes, unsigned long long hi_bytes, cudaStream_t s);
 
 // ---- graph-driven levels (tw_graph.cu) ---------------------------------------
 // Device state of a decide run whose level loop is a captured CUDA graph: a

@@ -158,20 +158,38 @@ template <class K>
 __global__ void __launch_bounds__(256)
     insert_ranges_kernel(const K* __restrict__ cand_key, const uint8_t* __restrict__ cand_v,
                          unsigned long long region_cap, const unsigned long long* __restrict__ prefix, int P,
-                         K* __restrict__ table, unsigned long long slots, int max_probes, K* __restrict__ out_keys,
+                         unsigned long long first_item, unsigned long long end_item, K* __restrict__ table,
+                         unsigned long long slots, int max_probes, K* __restrict__ out_keys,
                          uint8_t* __restrict__ out_pred, unsigned long long out_cap, LevelCounters* ctr) {
+  __shared__ unsigned long long sPrefix[kMaxRanges + 1];
+  for (int i = threadIdx.x; i <= P; i += blockDim.x) sPrefix[i] = prefix[i];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned lanemask_lt = (1u << lane) - 1u;
-  const unsigned long long total = prefix[P];
+  const unsigned long long total = end_item;
   const K empty = kones<K>();
   const unsigned long long warp_first =
-      ((unsigned long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32ull * kItemsPerThread;
-  if (warp_first >= total) return;
+      first_item + ((unsigned long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32ull * kItemsPerThread;
+  // (warps past the end stay for the block's output reservation below)
   K key[kItemsPerThread];
   int vv[kItemsPerThread];
   unsigned long long h[kItemsPerThread];
   int st[kItemsPerThread];
+  // range of the thread's first item: binary search in the shared prefix sums
+  // (the last r with sPrefix[r] <= item); later items only move forward
   int r = 0;
+  {
+    const unsigned long long j0 = warp_first + lane;
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sPrefix[mid] <= j0)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    r = lo;
+  }
 #pragma unroll
   for (int u = 0; u < kItemsPerThread; ++u) {
     const unsigned long long j = warp_first + (unsigned long long)u * 32ull + lane;
@@ -180,7 +198,7 @@ __global__ void __launch_bounds__(256)
     h[u] = 0;
     key[u] = kzero<K>();
     if (j < total) {
-      while (prefix[r + 1] <= j) ++r;
+      while (sPrefix[r + 1] <= j) ++r;
       const unsigned long long at = (unsigned long long)r * region_cap + (j - prefix[r]);
       key[u] = load_stream(&cand_key[at]);
       vv[u] = load_stream(&cand_v[at]);
@@ -226,10 +244,22 @@ __global__ void __launch_bounds__(256)
     wm[u] = __ballot_sync(kFull, st[u] == 2);
     wins += __popc(wm[u]);
   }
+  // one output reservation per block (a single counter takes every block's
+  // add, so fewer adds mean less serialisation at its L2 slice)
+  __shared__ int sWins[8];
+  __shared__ unsigned long long sBase;
+  const int warp = threadIdx.x >> 5;
+  if (lane == 0) sWins[warp] = wins;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += sWins[w2];
+    sBase = tot ? atomicAdd(&ctr->out_count, (unsigned long long)tot) : 0ull;
+  }
+  __syncthreads();
   if (wins) {
-    unsigned long long b = 0;
-    if (lane == 0) b = atomicAdd(&ctr->out_count, (unsigned long long)wins);
-    b = __shfl_sync(kFull, b, 0);
+    unsigned long long b = sBase;
+    for (int w2 = 0; w2 < warp; ++w2) b += (unsigned long long)sWins[w2];
 #pragma unroll
     for (int u = 0; u < kItemsPerThread; ++u) {
       if (st[u] == 2) {
@@ -243,6 +273,30 @@ __global__ void __launch_bounds__(256)
       }
       b += (unsigned long long)__popc(wm[u]);
     }
+  }
+}
+
+// Sets slots [first, first + count) of a table of `total` slots (wrapping at
+// the end) to the empty key.
+template <class K>
+__global__ void clear_slots_kernel(K* __restrict__ table, unsigned long long first, unsigned long long count,
+                                   unsigned long long total) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    unsigned long long j = first + i;
+    if (j >= total) j -= total;
+    table[j] = kones<K>();
+  }
+}
+
+// Drops the 128-byte lines of [lo, hi) from L2 without writing them back
+// (PTX discard.global.L2): a table slice whose range is complete is never
+// read again, and the next use of the table empties it first.
+__global__ void discard_lines_kernel(char* base, unsigned long long first_line, unsigned long long lines) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < lines; i += stride) {
+    char* line = base + (first_line + i) * 128ull;
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
   }
 }
 
@@ -284,13 +338,26 @@ cudaError_t emit_t(const ExpandLaunch& a, const PartitionBufs& pb, cudaStream_t 
 }
 
 template <class K>
-cudaError_t insert_t(const ExpandLaunch& a, const PartitionBufs& pb, unsigned long long total, cudaStream_t s) {
-  if (total == 0) return cudaSuccess;
+cudaError_t insert_t(const ExpandLaunch& a, const PartitionBufs& pb, unsigned long long first,
+                     unsigned long long end, cudaStream_t s) {
+  if (end <= first) return cudaSuccess;
   const unsigned long long per_block = 256ull * kItemsPerThread;
-  const unsigned long long blocks = (total + per_block - 1) / per_block;
+  const unsigned long long blocks = (end - first + per_block - 1) / per_block;
   insert_ranges_kernel<K><<<(unsigned)blocks, 256, 0, s>>>(
-      static_cast<const K*>(pb.cand_key), pb.cand_v, pb.region_cap, pb.prefix, pb.ranges, static_cast<K*>(a.table),
-      a.table_slots, a.max_probes, static_cast<K*>(a.out_keys), a.out_pred, a.out_cap, a.ctr);
+      static_cast<const K*>(pb.cand_key), pb.cand_v, pb.region_cap, pb.prefix, pb.ranges, first, end,
+      static_cast<K*>(a.table), a.table_slots, a.max_probes, static_cast<K*>(a.out_keys), a.out_pred, a.out_cap,
+      a.ctr);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t clear_slots_t(void* table, unsigned long long first, unsigned long long count, unsigned long long total,
+                          cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  unsigned long long g = (count + 1023) / 1024;
+  const unsigned long long cap = (unsigned long long)sm_count() * 8ull;
+  if (g > cap) g = cap;
+  clear_slots_kernel<K><<<(int)g, 256, 0, s>>>(static_cast<K*>(table), first, count, total);
   return cudaGetLastError();
 }
 
@@ -305,13 +372,32 @@ cudaError_t launch_emit(const ExpandLaunch& a, const PartitionBufs& pb, cudaStre
   }
 }
 
-cudaError_t launch_insert_ranges(const ExpandLaunch& a, const PartitionBufs& pb, unsigned long long total,
-                                 cudaStream_t s) {
+cudaError_t launch_insert_ranges(const ExpandLaunch& a, const PartitionBufs& pb, unsigned long long first,
+                                 unsigned long long end, cudaStream_t s) {
   switch (a.kc) {
-    case kKey32: return insert_t<uint32_t>(a, pb, total, s);
-    case kKey64: return insert_t<unsigned long long>(a, pb, total, s);
-    default: return insert_t<K128>(a, pb, total, s);
+    case kKey32: return insert_t<uint32_t>(a, pb, first, end, s);
+    case kKey64: return insert_t<unsigned long long>(a, pb, first, end, s);
+    default: return insert_t<K128>(a, pb, first, end, s);
   }
+}
+
+cudaError_t launch_clear_slots(KeyClass kc, void* table, unsigned long long first, unsigned long long count,
+                               unsigned long long total, cudaStream_t s) {
+  switch (kc) {
+    case kKey32: return clear_slots_t<uint32_t>(table, first, count, total, s);
+    case kKey64: return clear_slots_t<unsigned long long>(table, first, count, total, s);
+    default: return clear_slots_t<K128>(table, first, count, total, s);
+  }
+}
+
+cudaError_t launch_discard_l2(void* base, unsigned long long lo_bytes, unsigned long long hi_bytes, cudaStream_t s) {
+  const unsigned long long first = (lo_bytes + 127) / 128, last = hi_bytes / 128;  // whole lines inside
+  if (last <= first) return cudaSuccess;
+  unsigned long long g = (last - first + 255) / 256;
+  const unsigned long long cap = (unsigned long long)sm_count() * 8ull;
+  if (g > cap) g = cap;
+  discard_lines_kernel<<<(int)g, 256, 0, s>>>(static_cast<char*>(base), first, last - first);
+  return cudaGetLastError();
 }
 
 }  // namespace tw

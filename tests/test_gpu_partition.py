@@ -45,3 +45,19 @@ def test_partitioned_emit_in_chunks():
     with context(fingerprints=True, partition_table_mb=-2, mem_cap_bytes=96 << 20) as c:
         for k in (7, 8):
             assert_decide_matches(c, adj, k)
+
+
+def test_partitioned_tables_beyond_l2_match_direct():
+    # levels 7 -> 8 of the partial 10-tree at k = 10 have a 1.1 GB table: the
+    # range-by-range insert (slices emptied in L2, dropped without write-back)
+    # against the direct kernel and, for the first levels, the oracle
+    adj = gg.workload_pktree60()
+    with context(fingerprints=True, graph_levels=-1) as d, \
+            context(fingerprints=True, graph_levels=-1, partition_table_mb=64) as p:
+        a = d.decide_level(adj, k=10, level=8, count_only=True)
+        b = p.decide_level(adj, k=10, level=8, count_only=True)
+    assert a["count"] == b["count"] == 56_723_308
+    for key in ("level_size", "fp_sum", "fp_xor", "generated", "states_expanded"):
+        assert a["stats"][key] == b["stats"][key], key
+    pre = oracle.decide_prefix(adj, 10, 5, count_canonical=False)
+    assert b["stats"]["level_size"][:6] == pre["level_size"] and b["stats"]["fp_sum"][:6] == pre["fp_sum"]
