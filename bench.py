@@ -58,6 +58,11 @@ def parse():
                     help="keep finished levels in pinned host memory (tw_config.spill_levels)")
     ap.add_argument("--no-sub", action="store_true", help="skip the other workloads' sub-records")
     ap.add_argument("--in-core", action="store_true", help="pktree60: no out-of-core levels (stop at the cap)")
+    ap.add_argument("--plain", action="store_true", help="pktree60: without the clique skip")
+    ap.add_argument("--partition-mb", type=int, default=0,
+                    help="tw_config.partition_table_mb (0 = library default, -1 = never, -2 = every level)")
+    ap.add_argument("--graph-levels", type=int, default=0, help="tw_config.graph_levels (pktree60, gnp20)")
+    ap.add_argument("--fused-off", action="store_true", help="gnp20: the level loop instead of the fused launch")
     ap.add_argument("--ncu-record", nargs=2, metavar=("CSV", "FIRST_LEVEL"),
                     help="write profiles/expand_insert_rgg40_counters.json from an ncu CSV of consecutive "
                          "expand launches starting at FIRST_LEVEL, then exit")
@@ -489,14 +494,16 @@ def _line(metric, value, unit, args, config, extra):
 
 def run_gnp20(args):
     """G(20, 0.3) seed 0, 32-bit states: the sweep from the lower bound (k = 6,
-    7, 8) with ordering and tree decomposition; launch-latency bound."""
+    7, 8) with ordering and tree decomposition, by default in one fused launch
+    (--fused-off runs the level loop instead)."""
     import numpy as np
     import torch
     from paper_1709_09990_gb300 import graphgen as gg
     from paper_1709_09990_gb300 import native
     adj = gg.workload_gnp20()
     stream = torch.cuda.Stream()
-    ctx = native.Context(device=0, stream=stream.cuda_stream)  # graph-driven levels
+    ctx = native.Context(device=0, stream=stream.cuda_stream, fused_states=-1 if args.fused_off else 0,
+                         graph_levels=args.graph_levels)
     rows = torch.from_numpy(gg.to_rows_u64(adj).astype(np.int64)).cuda()
     for _ in range(args.warmup):
         ctx.solve(rows, n=20, want_td=True)
@@ -528,8 +535,9 @@ def run_pktree60(args):
     from paper_1709_09990_gb300 import native
     adj = gg.workload_pktree60()
     cap = int(args.mem_cap_gb * (1 << 30)) if args.mem_cap_gb else 150 << 30
-    with native.Context(device=0, mem_cap_bytes=cap, time_kernels=True, clique_skip=True,
-                        out_of_core=not args.in_core) as ctx:
+    with native.Context(device=0, mem_cap_bytes=cap, time_kernels=True, clique_skip=not args.plain,
+                        out_of_core=not args.in_core, partition_table_mb=args.partition_mb,
+                        graph_levels=args.graph_levels) as ctx:
         b = ctx.bounds(adj).tolist()
         t = time.perf_counter()
         r = ctx.decide(adj, k=10, raise_on_error=False)
@@ -537,9 +545,11 @@ def run_pktree60(args):
     st = r["stats"]
     answered = r["status"] == 0
     _line(METRIC, round(st["states_expanded"] / dt, 1), UNIT, args,
-          {"workload": "partial 10-tree n=60 (30% of edges removed) seed 0; decide at k=10 with the clique skip",
+          {"workload": "partial 10-tree n=60 (30% of edges removed) seed 0; decide at k=10"
+                       + ("" if args.plain else " with the clique skip"),
            "n": 60, "bounds": {"mmd": b[0], "mmd_plus": b[1], "min_degree_width": b[2], "min_fill_width": b[3]},
-           "mem_cap_gb": round(cap / (1 << 30), 1), "out_of_core": not args.in_core},
+           "mem_cap_gb": round(cap / (1 << 30), 1), "out_of_core": not args.in_core,
+           "partition_table_mb": args.partition_mb},
           {"status": native.strerror(r["status"]), "status_code": r["status"],
            "yes": r["yes"] if answered else None,
            "tw": 10 if answered and r["yes"] and max(b[0], b[1]) == 10 else None,

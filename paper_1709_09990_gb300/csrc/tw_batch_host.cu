@@ -519,9 +519,44 @@ struct DevMem {
 int run_batch_persistent(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
                          const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
                          std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st, std::vector<int>* evicted,
-                         const BatchDecide* dm) {
+                         const BatchDecide* dm, int warps);
+
+// With tw_config.autotune, the first batch of at least 512 graphs times the
+// persistent kernel with 4 and with 8 warps per block on a sample of 256 of
+// its graphs (every G/256-th) and keeps the faster choice for the context.
+int batch_warps(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
+                const std::vector<float>* hint, const std::vector<int64_t>& order_off, const BatchDecide* dm) {
+  if (c->batch_warps > 0) return c->batch_warps;
+  if (!c->cfg.autotune || idx.size() < 512) return 4;
+  std::vector<int> sample;
+  const size_t step = idx.size() / 256;
+  for (size_t j = 0; j < idx.size() && sample.size() < 256; j += step) sample.push_back(idx[j]);
+  std::vector<int> tw_tmp(graphs.size(), -1), st_tmp(graphs.size(), 0), ev;
+  double best = 1e30;
+  int best_w = 4;
+  for (int w : {4, 8}) {
+    ev.clear();
+    Timer t;
+    int rc = run_batch_persistent(c, graphs, sample, hint, order_off, tw_tmp.data(), nullptr, &st_tmp, nullptr, &ev,
+                                  dm, w);
+    if (rc) return 4;
+    const double secs = t.seconds();
+    if (secs < best) {
+      best = secs;
+      best_w = w;
+    }
+  }
+  c->batch_warps = best_w;
+  return best_w;
+}
+
+int run_batch_persistent(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
+                         const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
+                         std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st, std::vector<int>* evicted,
+                         const BatchDecide* dm, int warps) {
   const int G = (int)idx.size();
   if (G == 0) return TW_OK;
+  if (warps == 0) warps = batch_warps(c, graphs, idx, hint, order_off, dm);
   NvtxRange range("tw batch persistent graphs=%d", G);
   std::vector<int> q(idx);
   std::stable_sort(q.begin(), q.end(), [&](int a, int b) { return graphs[a].n > graphs[b].n; });
@@ -537,7 +572,6 @@ int run_batch_persistent(tw_ctx* c, const std::vector<HostGraph>& graphs, const 
     ooff[j] = order_off[q[j]];
     total_n = std::max<int64_t>(total_n, ooff[j] + hg.n);
   }
-  const int warps = 4;
   const int blocks = batch_solve_blocks(warps);
   // workspace: per block A keys and predecessor bytes, two tables of 2A slots
   const size_t room = c->mem_cap > total_bytes(c) ? c->mem_cap - total_bytes(c) : 0;
@@ -675,7 +709,7 @@ int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::
   for (int i : idx) (graphs[i].n <= 64 ? small : single).push_back(i);
   int rc = c->cfg.batch_kernel == 1 ? run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single, nullptr)
                                     : run_batch_persistent(c, graphs, small, hint, order_off, htw, hord, hst, st, &single,
-                                                           nullptr);
+                                                           nullptr, 0);
   if (rc) return rc;
   for (int gi : single) {
     const HostGraph& hg = graphs[gi];
@@ -739,7 +773,8 @@ int decide_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std:
   std::vector<int> htw(graphs.size(), -1);
   int rc = c->cfg.batch_kernel == 1
                ? run_batch(c, graphs, small, nullptr, order_off, htw.data(), nullptr, hst, st, &single, &dm)
-               : run_batch_persistent(c, graphs, small, nullptr, order_off, htw.data(), nullptr, hst, st, &single, &dm);
+               : run_batch_persistent(c, graphs, small, nullptr, order_off, htw.data(), nullptr, hst, st, &single, &dm,
+                                      0);
   if (rc) return rc;
   const tw_config saved = c->cfg;
   c->cfg.clique_skip = c->cfg.disjoint_paths = c->cfg.mmw_prune = 0;

@@ -83,6 +83,7 @@ struct tw_ctx {
     int kc, nb, block_threads, load_pct;
   };
   std::vector<Tuned> tuned;
+  int batch_warps = 0;  // warps per block of the persistent batch kernel (autotuned once)
   // pinned host chunks that hold finished levels with spill_levels; reused
   // from the start by every decide run
   struct HostChunk {

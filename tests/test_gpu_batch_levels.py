@@ -111,3 +111,21 @@ def test_persistent_batch_equals_level_synchronous_and_loop():
         b = sync.solve_batch(small)
     assert a["tw"].tolist() == b["tw"].tolist()
     assert a["stats"]["kernel_launches"] == 2 < b["stats"]["kernel_launches"]
+
+
+def test_autotuned_persistent_batch_is_exact():
+    # the first batch of >= 512 graphs picks 4 or 8 warps per block on a
+    # sample; the answers do not depend on the choice
+    graphs = [gg.mixed_graph(7000 + j, 10, 22, j % 2 == 0) for j in range(600)]
+    with context(autotune=True) as tuned, context() as plain:
+        a = tuned.solve_batch(graphs)
+        b = plain.solve_batch(graphs)
+        c2 = tuned.solve_batch(graphs[:50])  # the choice is kept for later batches
+    assert a["status"] == 0 and b["status"] == 0 and c2["status"] == 0
+    assert a["tw"].tolist() == b["tw"].tolist()
+    assert c2["tw"].tolist() == b["tw"].tolist()[:50]
+    pos = 0
+    for g, adj in enumerate(graphs[:120]):
+        order = a["orders"][pos: pos + len(adj)].tolist()
+        assert oracle.width_elim(adj, order) == int(b["tw"][g])
+        pos += len(adj)
