@@ -58,6 +58,9 @@ def parse():
                     help="keep finished levels in pinned host memory (tw_config.spill_levels)")
     ap.add_argument("--no-sub", action="store_true", help="skip the other workloads' sub-records")
     ap.add_argument("--in-core", action="store_true", help="pktree60: no out-of-core levels (stop at the cap)")
+    ap.add_argument("--host-cap-gb", type=float, default=0.0,
+                    help="pktree60: pinned host memory for out-of-core levels (0 = 85%% of the memory this "
+                         "process may use: MemAvailable, or the cgroup limit when lower)")
     ap.add_argument("--plain", action="store_true", help="pktree60: without the clique skip")
     ap.add_argument("--partition-mb", type=int, default=0,
                     help="tw_config.partition_table_mb (0 = library default, -1 = never, -2 = every level)")
@@ -525,6 +528,31 @@ def run_gnp20(args):
     ctx.close()
 
 
+def host_cap_mb(args) -> int:
+    """Pinned host memory (MB) the out-of-core levels may take: --host-cap-gb,
+    else 85% of what this process may use (MemAvailable, or the cgroup's
+    memory limit minus its current use when that is lower)."""
+    if args.host_cap_gb:
+        return int(args.host_cap_gb * 1024)
+    avail = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    for lim, cur in (("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory.current"),
+                     ("/sys/fs/cgroup/memory/memory.limit_in_bytes", "/sys/fs/cgroup/memory/memory.usage_in_bytes")):
+        try:
+            v = open(lim).read().strip()
+            if v.isdigit() and int(v) < (1 << 60):
+                room = int(v) - int(open(cur).read().strip())
+                avail = room if avail is None else min(avail, room)
+        except (OSError, ValueError):
+            pass
+    return int(0.85 * avail) >> 20 if avail else 0
+
+
 def run_pktree60(args):
     """Partial 10-tree n=60 seed 0: decide at k = 10 (the lower bound MMD+ =
     10 certifies no at k = 9) with the Section 3.1 clique skip and out-of-core
@@ -535,9 +563,10 @@ def run_pktree60(args):
     from paper_1709_09990_gb300 import native
     adj = gg.workload_pktree60()
     cap = int(args.mem_cap_gb * (1 << 30)) if args.mem_cap_gb else 150 << 30
+    hcap = host_cap_mb(args)
     with native.Context(device=0, mem_cap_bytes=cap, time_kernels=True, clique_skip=not args.plain,
                         out_of_core=not args.in_core, partition_table_mb=args.partition_mb,
-                        graph_levels=args.graph_levels) as ctx:
+                        graph_levels=args.graph_levels, host_cap_mb=hcap) as ctx:
         b = ctx.bounds(adj).tolist()
         t = time.perf_counter()
         r = ctx.decide(adj, k=10, raise_on_error=False)
@@ -549,6 +578,7 @@ def run_pktree60(args):
                        + ("" if args.plain else " with the clique skip"),
            "n": 60, "bounds": {"mmd": b[0], "mmd_plus": b[1], "min_degree_width": b[2], "min_fill_width": b[3]},
            "mem_cap_gb": round(cap / (1 << 30), 1), "out_of_core": not args.in_core,
+           "host_cap_gb": round(hcap / 1024, 1),
            "partition_table_mb": args.partition_mb},
           {"status": native.strerror(r["status"]), "status_code": r["status"],
            "yes": r["yes"] if answered else None,

@@ -120,16 +120,21 @@ typedef struct {
                              table is built in slices, one hash range at a time,
                              each slice small enough for the cap (the level's
                              search repeats once per slice), and a level that
-                             does not fit the device is written to pinned host
-                             memory (Grace memory over NVLink-C2C on GB300) and
-                             read from there by the next level.  Results are
-                             unchanged.  tw_decide without order, tw_decide_level
-                             and the decide runs of tw_solve without outputs use
-                             it; a failed host allocation is TW_ERR_CAPACITY.    */
+                             does not fit the device next to its input and table
+                             is written, wholly or in part, to pinned host
+                             memory (Grace memory over NVLink-C2C on GB300; up
+                             to host_cap_mb) and read from there by the next
+                             level.  Results are unchanged.  tw_decide without
+                             order, tw_decide_level and the decide runs of
+                             tw_solve without outputs use it; a failed host
+                             allocation is TW_ERR_CAPACITY.                      */
   int fused_states;       /* tw_solve / tw_decide on graphs with n <= 64 first run
                              the whole k sweep, walk and tree decomposition in one
-                             cooperative launch (grid barriers between levels)
-                             whose level arena holds this many states; a run
+                             cooperative launch (barriers between levels; the
+                             decide runs k, k+1, k+2 of the sweep run at once in
+                             three groups of blocks, and the first of them that
+                             does not answer no decides, as in the sequential
+                             sweep) whose level arenas hold this many states; a run
                              whose levels outgrow it goes on with the level loop
                              from the k it reached.  0 = 2^20 states (the
                              default), -1 = never.  Not used with clique_skip,
@@ -141,6 +146,8 @@ typedef struct {
                              1 = level-synchronous steps, one launch per step for
                              the current level of every running graph.  Results
                              are unchanged.                                      */
+  int host_cap_mb;        /* out_of_core: pinned host memory, in MB, that levels
+                             may occupy; 0 = 85% of the host's physical memory  */
   int reserved[1];        /* must be zero                                         */
 } tw_config;
 

@@ -122,34 +122,50 @@ int run_level_partitioned(tw_ctx* c, const ExpandLaunch& a, int cand_per_state, 
 // ---- out-of-core levels (tw_config.out_of_core) ------------------------------
 //
 // A decide run without ordering keeps only two levels: the one being expanded
-// and the one being built.  When one of them or the level's table would not
+// and the one being built.  When they and the level's hash table would not
 // fit the memory cap, the run goes on here:
-//  * the new level goes to the device arena if it fits there next to the
-//    input level and a table slice of reasonable size, else to one of two
-//    pinned, device-mapped host buffers (the one not holding the input), and
-//    the next level reads it from there;
+//  * a level may be split: a device part (in one of two device buffers) and a
+//    host part (in one of two pinned, device-mapped host buffers, Grace memory
+//    on GB300, read and written by the kernels over NVLink-C2C).  The new
+//    level fills the host buffer the input does not use first, up to the host
+//    limit, and the rest goes to the device, so that the device keeps as much
+//    room as possible for the table;
 //  * the level's table is split into P hash ranges: each pass empties a slice
-//    that fits what the cap leaves, expands the whole input level and inserts
-//    only the pairs whose hash falls in its range (the ranged kernel), so the
-//    passes together insert every pair once.
+//    that fits what the cap leaves, expands the whole input level (each of its
+//    parts) and inserts only the pairs whose hash falls in its range (the
+//    ranged kernel), so the passes together insert every pair once.  A pass
+//    writes its new sets to the host part while that has room for it, else to
+//    the device part; a pass whose output overflows its part is redone on its
+//    own into the other part.
 // Level sets, sizes and counters are those of the in-memory run; the input is
 // read and searched once per pass.
 
-// Host buffer hb of the context, grown to at least bytes; *dptr is its
-// device-side address.
+// Pinned host bytes that out-of-core levels may occupy.
+size_t ooc_host_limit(const tw_ctx* c) {
+  if (c->cfg.host_cap_mb > 0) return (size_t)c->cfg.host_cap_mb << 20;
+  const size_t phys = (size_t)sysconf(_SC_PHYS_PAGES) * (size_t)sysconf(_SC_PAGESIZE);
+  return phys / 20 * 17;
+}
+
+// Frees host buffer hb (its level is no longer needed).
+void release_host(tw_ctx* c, int hb) {
+  tw_ctx::HostChunk& ch = c->ooc_host[hb];
+  if (!ch.ptr) return;
+  cudaStreamSynchronize(c->stream);
+  cudaFreeHost(ch.ptr);
+  ch = {nullptr, nullptr, 0};
+}
+
+// Host buffer hb of the context, grown to at least bytes (whole MiB); *dptr
+// is its device-side address.  Both buffers together stay within the host
+// limit.
 int ooc_host_buffer(tw_ctx* c, int hb, size_t bytes, char** dptr) {
   tw_ctx::HostChunk& ch = c->ooc_host[hb];
   if (ch.bytes < bytes) {
-    // both buffers together stay within 85% of the host's physical memory
-    const size_t phys = (size_t)sysconf(_SC_PHYS_PAGES) * (size_t)sysconf(_SC_PAGESIZE);
-    if (bytes + c->ooc_host[1 - hb].bytes > phys / 20 * 17) return TW_ERR_CAPACITY;
-    if (ch.ptr) {
-      TW_CK(cudaStreamSynchronize(c->stream));
-      cudaFreeHost(ch.ptr);
-      ch = {nullptr, nullptr, 0};
-    }
-    const size_t gib = size_t(1) << 30;
-    const size_t want = (bytes + gib - 1) / gib * gib;
+    const size_t mib = size_t(1) << 20;
+    const size_t want = (bytes + mib - 1) / mib * mib;
+    if (want + c->ooc_host[1 - hb].bytes > ooc_host_limit(c)) return TW_ERR_CAPACITY;
+    release_host(c, hb);
     void* p = nullptr;
     if (cudaHostAlloc(&p, want, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
       cudaGetLastError();
@@ -191,12 +207,17 @@ bool alloc_exact(tw_ctx* c, DevBuf* b, size_t bytes) {
   return true;
 }
 
+// Where one out-of-core level lives: dcount keys in device buffer db from
+// offset off, then hcount keys at the start of host buffer hb.
+struct OocLevel {
+  int db = 0;
+  unsigned long long off = 0, dcount = 0;
+  int hb = -1;
+  unsigned long long hcount = 0;
+};
+
 // Continues decide(k) out of core from the last level of R (on the device in
-// the level arena at its offset).  Levels live in one of two device buffers
-// (the level arena and c->ooc_keys) or one of two host buffers; the new level
-// goes to the device buffer that does not hold the input when it fits there
-// with a table slice, else to the host buffer that does not hold the input.
-// stop_level as in run_decide.
+// the level arena at its offset).  stop_level as in run_decide.
 int run_decide_ooc(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, int stop_level) {
   NvtxRange range("tw decide out of core n=%d k=%d", n, k);
   const size_t w = key_bytes(kc);
@@ -204,60 +225,85 @@ int run_decide_ooc(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, int st
   release(c, &c->pred);
   release(c, &c->cand_key);
   release(c, &c->cand_v);
+  if (!c->d_ctr_host) TW_CK(cudaMalloc(reinterpret_cast<void**>(&c->d_ctr_host), sizeof(LevelCounters)));
   DevBuf* dev[2] = {&c->keys, &c->ooc_keys};
+  LevelCounters* d_ctr[2] = {c->d_ctr, c->d_ctr_host};  // [0]: device part, [1]: host part
   const int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 75;
   const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
   const size_t margin = std::min<size_t>(64ull << 20, c->mem_cap / 16);
-  int in_dev = 0, in_host = -1;  // where the input level is (device or host buffer)
+  const size_t host_limit = ooc_host_limit(c);
+  const bool timed = c->cfg.time_kernels != 0;
+  OocLevel in;
+  in.off = R->levels.back().off;
+  in.dcount = R->levels.back().count;
   for (int i = (int)R->levels.size() - 1; i <= n - k - 2; ++i) {
     if (stop_level >= 0 && i >= stop_level) break;
-    const LevelRec cur = R->levels[i];
-    if (cur.count == 0) break;
-    const double bound = std::min((double)cur.count * (double)(n - i), binom(n, i + 1)) + 1.0;
-    double est = (double)cur.count;
+    const unsigned long long cur_count = R->levels[i].count;
+    if (cur_count == 0) break;
+    // size estimate of the new level: the last growth ratio, lowered by half
+    // of its last fall (geometric mean) while the ratios fall
+    const double bound = std::min((double)cur_count * (double)(n - i), binom(n, i + 1)) + 1.0;
+    double est = (double)cur_count;
     if (i > 0 && R->levels[i - 1].count > 0) {
-      double r = (double)cur.count / (double)R->levels[i - 1].count;
+      double r = (double)cur_count / (double)R->levels[i - 1].count;
+      if (i > 1 && R->levels[i - 2].count > 0) {
+        const double r_prev = (double)R->levels[i - 1].count / (double)R->levels[i - 2].count;
+        if (r < r_prev) r *= std::sqrt(std::max(0.25, r / r_prev));
+      }
       r = std::min(std::max(r, 0.25), (double)(n - i));
-      est = (double)cur.count * r;
+      est = (double)cur_count * r;
     }
-    double out_est = std::min(bound, est * 1.10 + 4096.0);
-    const char* in_ptr =
-        in_host >= 0 ? c->ooc_host[in_host].dptr : static_cast<char*>(dev[in_dev]->ptr) + cur.off * w;
-    if (in_host >= 0) {
-      release(c, dev[0]);
-      release(c, dev[1]);
-    }
-    LevelRec nxt;
-    unsigned long long generated = 0;
-    int passes = 0, out_dev = -1, out_host = -1;
+    double out_est = std::min(bound, est * 1.04 + 4096.0);
+    // the parts of the input
+    const char* in_part[2] = {
+        in.dcount ? static_cast<const char*>(dev[in.db]->ptr) + in.off * w : nullptr,
+        in.hcount ? c->ooc_host[in.hb].dptr : nullptr};
+    const unsigned long long in_cnt[2] = {in.dcount, in.hcount};
+    // buffers the new level may use: those the input does not hold
+    const int od = in.dcount ? 1 - in.db : 0;
+    if (!in.dcount) release(c, dev[1]);
+    const int oh = in.hcount ? 1 - in.hb : (c->ooc_host[1].bytes > c->ooc_host[0].bytes ? 1 : 0);
+    if (!in.hcount) release_host(c, 1 - oh);
+    OocLevel nxt;
+    unsigned long long generated = 0, launches = 0;
     float ms_total = 0.f;
     for (int attempt = 0;; ++attempt) {
       if (attempt > 16) return TW_ERR_CAPACITY;
+      if (attempt > 0) ++R->retries;
       const unsigned long long out_cap = (unsigned long long)std::ceil(out_est);
       release(c, &c->table);
+      release(c, dev[od]);
       const unsigned long long total_slots =
           std::max<unsigned long long>(1024ull, (unsigned long long)std::ceil(out_est * 100.0 / load_pct));
       const size_t table_bytes = (size_t)total_slots * w;
-      const size_t min_slice = std::max<size_t>(std::min<size_t>(512ull << 20, c->mem_cap / 4), table_bytes / 64);
-      // the new level: on the device buffer the input does not use, if it
-      // fits there with a table slice; else in host memory
-      out_dev = in_host >= 0 ? 0 : 1 - in_dev;
-      out_host = -1;
-      release(c, dev[out_dev]);
-      const size_t out_bytes = std::max<size_t>(256, (size_t)out_cap * w);
-      char* out_ptr = nullptr;
-      if (total_bytes(c) + out_bytes + min_slice + margin <= c->mem_cap && alloc_exact(c, dev[out_dev], out_bytes)) {
-        out_ptr = static_cast<char*>(dev[out_dev]->ptr);
-      } else {
-        out_dev = -1;
-        out_host = in_host >= 0 ? 1 - in_host : 0;
-        int rc = ooc_host_buffer(c, out_host, out_bytes, &out_ptr);
+      const size_t small_slice = std::max<size_t>(std::min<size_t>(256ull << 20, c->mem_cap / 8), table_bytes / 512);
+      if (total_bytes(c) + margin + small_slice > c->mem_cap) return TW_ERR_CAPACITY;
+      const size_t dev_room = c->mem_cap - total_bytes(c) - margin;
+      // placement: all on the device when the level and its whole table fit
+      // there; else as much of it as the host limit allows in host memory
+      unsigned long long cap_part[2] = {out_cap, 0};
+      if ((size_t)out_cap * w + table_bytes + 16384 > dev_room) {
+        const size_t in_host_bytes = in.hcount ? c->ooc_host[in.hb].bytes : 0;
+        const size_t host_room = host_limit > in_host_bytes ? (host_limit - in_host_bytes) & ~((size_t(1) << 20) - 1) : 0;
+        // (the host part also takes up to 10% more than the estimate, which
+        // costs the device nothing)
+        const unsigned long long on_host = std::min<unsigned long long>(out_cap, host_room / w);
+        cap_part[0] = out_cap - on_host;
+        cap_part[1] = std::min<unsigned long long>(host_room / w, on_host + out_cap / 10);
+        if ((size_t)cap_part[0] * w + small_slice > dev_room) return TW_ERR_CAPACITY;
+      }
+      char* out_part[2] = {nullptr, nullptr};
+      if (cap_part[0]) {
+        if (!alloc_exact(c, dev[od], (size_t)cap_part[0] * w)) return TW_ERR_CAPACITY;
+        out_part[0] = static_cast<char*>(dev[od]->ptr);
+      }
+      if (cap_part[1]) {
+        int rc = ooc_host_buffer(c, oh, (size_t)cap_part[1] * w, &out_part[1]);
         if (rc) return rc;
       }
       // the table: as many hash-range passes as the cap needs
-      const size_t dev_used = total_bytes(c) + margin;
-      if (dev_used + 16384 > c->mem_cap) return TW_ERR_CAPACITY;
-      const size_t slice_budget = c->mem_cap - dev_used;
+      if (total_bytes(c) + margin + 16384 > c->mem_cap) return TW_ERR_CAPACITY;
+      const size_t slice_budget = c->mem_cap - total_bytes(c) - margin;
       unsigned long long P = std::max<unsigned long long>(1ull, (table_bytes + slice_budget - 1) / slice_budget);
       unsigned long long slice_slots = 0;
       size_t slice_bytes = 0;
@@ -267,93 +313,134 @@ int run_decide_ooc(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, int st
         slice_bytes = (size_t)((slice_slots * w + 15) & ~15ull);
         if (alloc_exact(c, &c->table, slice_bytes)) break;
       }
-      const bool timed = c->cfg.time_kernels != 0;
-      bool table_full = false;
-      unsigned long long before = 0;
-      LevelCounters h{};
+      // both counter blocks start at zero; the host keeps their values after
+      // every pass so that a pass can be redone from them
+      TW_CK(cudaMemsetAsync(c->d_ctr_host, 0, sizeof(LevelCounters), c->stream));
+      TW_CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(LevelCounters), c->stream));
+      LevelCounters done[2] = {LevelCounters{}, LevelCounters{}};
+      bool replan = false;
       ms_total = 0.f;
-      for (unsigned long long r = 0; r < P; ++r) {
-        TW_LAUNCH(c, launch_clear(c->table.ptr, slice_bytes, r == 0 ? c->d_ctr : nullptr, c->stream));
-        ExpandLaunch a;
-        a.kc = kc;
-        a.in_keys = in_ptr;
-        a.n_in = cur.count;
-        a.adj = small_at(c, L.adj);
-        a.n = n;
-        a.k = k;
-        a.table = c->table.ptr;
-        a.table_slots = slice_slots;
-        a.max_probes = max_probes;
-        a.out_keys = out_ptr;
-        a.out_pred = nullptr;
-        a.out_cap = out_cap;
-        a.ctr = c->d_ctr;
-        a.block_threads = 128;
-        a.grid = 0;
-        a.allowed[0] = c->allowed[0];
-        a.allowed[1] = c->allowed[1];
-        a.mmw = 0;
-        a.ranges = P;
-        a.range = r;
-        if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
-        TW_LAUNCH(c, launch_expand(a, c->stream));
-        if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
-        TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
-        TW_CK(cudaStreamSynchronize(c->stream));
-        h = *c->h_ctr;
-        if (timed) {
-          float ms = 0.f;
-          TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-          ms_total += ms;
-        }
-        const unsigned long long got = h.out_count - before;
-        before = h.out_count;
-        if ((h.overflow & 2u) || got * 100ull > slice_slots * 90ull) {
-          // this range held more than its slice: more states than estimated
-          table_full = true;
-          const double projected = (double)h.out_count / (double)(r + 1) * (double)P;
-          out_est = std::max(out_est * 1.5, projected * 1.2);
+      launches = 0;
+      for (unsigned long long r = 0; r < P && !replan; ++r) {
+        // the part this pass writes to: the host part while it has room for
+        // a pass of the size seen so far, else the device part
+        const unsigned long long so_far = done[0].out_count + done[1].out_count;
+        const double expect = (r > 0 ? (double)so_far / (double)r : out_est / (double)P) * 1.15 + 4096.0;
+        int part = (cap_part[1] > done[1].out_count && (double)(cap_part[1] - done[1].out_count) >= expect) ? 1 : 0;
+        if (part == 0 && cap_part[0] <= done[0].out_count) part = 1;
+        for (int redo = 0;; ++redo) {
+          TW_LAUNCH(c, launch_clear(c->table.ptr, slice_bytes, nullptr, c->stream));
+          if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
+          for (int ip = 0; ip < 2; ++ip) {
+            if (!in_cnt[ip]) continue;
+            ExpandLaunch a;
+            a.kc = kc;
+            a.in_keys = in_part[ip];
+            a.n_in = in_cnt[ip];
+            a.adj = small_at(c, L.adj);
+            a.n = n;
+            a.k = k;
+            a.table = c->table.ptr;
+            a.table_slots = slice_slots;
+            a.max_probes = max_probes;
+            a.out_keys = out_part[part];
+            a.out_pred = nullptr;
+            a.out_cap = cap_part[part];
+            a.ctr = d_ctr[part];
+            a.block_threads = 128;
+            a.grid = 0;
+            a.allowed[0] = c->allowed[0];
+            a.allowed[1] = c->allowed[1];
+            a.mmw = 0;
+            a.ranges = P;
+            a.range = r;
+            TW_LAUNCH(c, launch_expand(a, c->stream));
+            ++launches;
+          }
+          if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
+          TW_CK(cudaMemcpyAsync(c->h_ctr, d_ctr[part], sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+          TW_CK(cudaStreamSynchronize(c->stream));
+          const LevelCounters h = *c->h_ctr;
+          if (timed) {
+            float ms = 0.f;
+            TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            ms_total += ms;
+          }
+          const unsigned long long got = h.out_count - done[part].out_count;
+          if ((h.overflow & 2u) || got * 100ull > slice_slots * 90ull) {
+            // this range held more than its slice: more states than estimated
+            const double projected = (double)(so_far + got) / (double)(r + 1) * (double)P;
+            out_est = std::max(out_est * 1.25, projected * 1.1);
+            replan = true;
+            break;
+          }
+          if (!(h.overflow & 1u)) {
+            done[part] = h;
+            break;
+          }
+          // the part filled up: undo this pass's counts and redo it into the
+          // other part if that has room for it, else plan the level again
+          TW_CK(cudaMemcpyAsync(d_ctr[part], &done[part], sizeof(LevelCounters), cudaMemcpyHostToDevice,
+                                c->stream));
+          const int other = 1 - part;
+          if (redo == 0 && cap_part[other] > done[other].out_count && cap_part[other] - done[other].out_count >= got) {
+            part = other;
+            continue;
+          }
+          const double projected = (double)(so_far + got) / (double)(r + 1) * (double)P;
+          out_est = std::max(out_est * 1.05, projected * 1.05);
+          replan = true;
           break;
         }
       }
-      if (attempt > 0) ++R->retries;
-      if (table_full) continue;
-      if (h.overflow & 1u) {
-        out_est = (double)h.out_count;  // exact: every range was inserted completely
-        continue;
-      }
+      if (replan) continue;
+      nxt.db = od;
       nxt.off = 0;
-      nxt.count = h.out_count;
-      nxt.hkeys = out_host >= 0 ? out_ptr : nullptr;
-      generated = h.generated;
-      passes = (int)P;
+      nxt.dcount = done[0].out_count;
+      nxt.hb = oh;
+      nxt.hcount = done[1].out_count;
+      generated = done[0].generated + done[1].generated;
       R->peak_bytes = std::max<unsigned long long>(R->peak_bytes, total_bytes(c));
       break;
     }
-    R->states_expanded += cur.count;
-    R->candidates += cur.count * (unsigned long long)(n - c->skipped - i);
+    const unsigned long long nxt_count = nxt.dcount + nxt.hcount;
+    R->states_expanded += cur_count;
+    R->candidates += cur_count * (unsigned long long)(n - c->skipped - i);
     R->generated += generated;
-    R->expand_launches += (unsigned long long)passes;
+    R->expand_launches += launches;
     R->expand_seconds += (double)ms_total * 1e-3;
-    R->expand_bytes += (double)(cur.count + generated + 2ull * nxt.count) * (double)w;
-    R->levels.push_back(nxt);
-    const char* out_keys = out_host >= 0 ? c->ooc_host[out_host].dptr : static_cast<char*>(dev[out_dev]->ptr);
-    in_dev = out_dev;
-    in_host = out_host;
+    R->expand_bytes += (double)(cur_count + generated + 2ull * nxt_count) * (double)w;
+    LevelRec rec;
+    rec.off = 0;
+    rec.count = nxt_count;
+    if (nxt.dcount == 0 && nxt.hcount > 0) {
+      rec.hkeys = c->ooc_host[nxt.hb].dptr;
+    } else if (nxt.hcount > 0) {
+      rec.htail = c->ooc_host[nxt.hb].dptr;
+      rec.tail = nxt.hcount;
+    }
+    R->levels.push_back(rec);
     if (c->cfg.fingerprints) {
-      TW_LAUNCH(c, launch_fingerprint(kc, out_keys, nxt.count, c->d_ctr, c->stream));
+      TW_CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(LevelCounters), c->stream));
+      if (nxt.dcount) TW_LAUNCH(c, launch_fingerprint(kc, dev[nxt.db]->ptr, nxt.dcount, c->d_ctr, c->stream));
+      if (nxt.hcount)
+        TW_LAUNCH(c, launch_fingerprint(kc, c->ooc_host[nxt.hb].dptr, nxt.hcount, c->d_ctr, c->stream));
       TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
       TW_CK(cudaStreamSynchronize(c->stream));
       R->fp_sum.push_back(c->h_ctr->fp_sum);
       R->fp_xor.push_back(c->h_ctr->fp_xor);
     }
-    if (nxt.count == 0) break;
+    // the input's buffers are free now; drop an empty device part's buffer
+    in = nxt;
+    if (!in.dcount) release(c, dev[in.db]);
+    if (nxt_count == 0) break;
   }
   const int last = (int)R->levels.size() - 1;
   R->yes = (last == n - k - 1 && R->levels[last].count > 0) ? 1 : 0;
   // device level records refer to the level arena (callers read the last
-  // level only): make the buffer that holds the last level the arena
-  if (in_host < 0 && in_dev == 1) std::swap(c->keys, c->ooc_keys);
+  // level only): make the buffer that holds the last level's device part the
+  // arena
+  if (in.dcount && in.db == 1) std::swap(c->keys, c->ooc_keys);
   return TW_OK;
 }
 
@@ -986,22 +1073,29 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
               int* answer_k, int* bail_k, tw_stats* st) {
   NvtxRange range("tw fused solve n=%d k0=%d", g.n, k0);
   const size_t w = key_bytes(kc);
+  // decide runs in flight at once: k0, k0+1, k0+2 (the sweep from a lower
+  // bound usually ends within a few k)
+  constexpr int kGroups = 3;
+  const int G = std::max(1, std::min(kGroups, k_last - k0 + 1));
   const unsigned long long A =
       c->cfg.fused_states > 0 ? (unsigned long long)c->cfg.fused_states : (1ull << 20);
   const unsigned long long T = 2 * A + 1024;
   const size_t st_bytes = (sizeof(FusedState) + 255) & ~size_t(255);
   const size_t tb = ((size_t)T * 8 + 255) & ~size_t(255);  // sized for 64-bit states
   const size_t kb = ((size_t)A * 8 + 255) & ~size_t(255);
-  const size_t need = st_bytes + 2 * tb + kb + A;
+  const size_t pb = ((size_t)A + 255) & ~size_t(255);
+  const size_t group_bytes = st_bytes + 2 * tb + kb + pb;
+  const size_t need = (size_t)kFusedMaxGroups * group_bytes;
   *status = 0;
   if (c->fused.bytes < need) {
+    c->fused_clean = false;
     int rc = grow(c, &c->fused, need, 0);
     if (rc == TW_ERR_CAPACITY) return TW_OK;  // no room under the cap: the level loop runs instead
     if (rc) return rc;
   }
   if (!c->h_fused) {
-    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_fused), sizeof(FusedState), cudaHostAllocDefault) !=
-        cudaSuccess) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_fused), kFusedMaxGroups * sizeof(FusedState),
+                      cudaHostAllocDefault) != cudaSuccess) {
       c->h_fused = nullptr;
       cudaGetLastError();
       return TW_ERR_CUDA;
@@ -1019,25 +1113,38 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
   f.k_last = k_last;
   f.max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
   f.load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
-  f.st = reinterpret_cast<FusedState*>(base);
-  f.table0 = base + st_bytes;
-  f.table1 = base + st_bytes + tb;
-  f.keys = base + st_bytes + 2 * tb;
-  f.pred = reinterpret_cast<uint8_t*>(base + st_bytes + 2 * tb + kb);
+  f.groups = G;
+  for (int j = 0; j < kFusedMaxGroups; ++j) {
+    char* gbase = base + (size_t)j * group_bytes;
+    f.st[j] = reinterpret_cast<FusedState*>(gbase);
+    f.table0[j] = gbase + st_bytes;
+    f.table1[j] = gbase + st_bytes + tb;
+    f.keys[j] = gbase + st_bytes + 2 * tb;
+    f.pred[j] = reinterpret_cast<uint8_t*>(gbase + st_bytes + 2 * tb + kb);
+  }
   f.arena_cap = A;
   f.table_cap = T;
   f.order = reinterpret_cast<int32_t*>(small_at(c, L.order));
   f.parent = reinterpret_cast<int32_t*>(small_at(c, L.parent));
   f.bags = reinterpret_cast<unsigned long long*>(small_at(c, L.bags));
-  TW_CK(cudaMemsetAsync(f.st, 0, sizeof(FusedState), c->stream));
+  if (!c->fused_clean) {
+    // a new buffer, or one a launch left early: empty every group's tables
+    // (all ones) once; launches that run to their end leave them empty
+    for (int j = 0; j < kFusedMaxGroups; ++j)
+      TW_CK(cudaMemsetAsync(f.table0[j], 0xff, 2 * tb, c->stream));
+    c->fused_clean = true;
+  }
+  f.tables_clean = 1;
+  for (int j = 0; j < G; ++j) TW_CK(cudaMemsetAsync(f.st[j], 0, sizeof(FusedState), c->stream));
   const bool timed = c->cfg.time_kernels != 0;
   if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
   TW_LAUNCH(c, launch_fused_solve(f, c->stream));
   if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
-  TW_CK(cudaMemcpyAsync(c->h_fused, f.st, sizeof(FusedState), cudaMemcpyDeviceToHost, c->stream));
+  TW_CK(cudaMemcpyAsync(c->h_fused, f.st[0], sizeof(FusedState), cudaMemcpyDeviceToHost, c->stream));
   TW_CK(cudaStreamSynchronize(c->stream));
   const FusedState& h = *c->h_fused;
-  if (h.error) return TW_ERR_TIMEOUT;  // a grid barrier wait gave up
+  c->fused_clean = h.error == 0u;  // a launch that ran to its end empties the tables it used
+  if (h.error) return TW_ERR_TIMEOUT;  // a barrier wait gave up
   *status = h.status;
   if (h.status != 1) {
     *bail_k = h.last;
@@ -1051,10 +1158,18 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
     }
     return TW_OK;
   }
+  // the levels of the deciding run are in its group's state and arena
+  const int grp = std::min(std::max(h.group, 0), G - 1);
+  const FusedState* hl = &h;
+  if (grp != 0) {
+    TW_CK(cudaMemcpyAsync(c->h_fused + 1, f.st[grp], sizeof(FusedState), cudaMemcpyDeviceToHost, c->stream));
+    TW_CK(cudaStreamSynchronize(c->stream));
+    hl = c->h_fused + 1;
+  }
   *answer_k = h.tw;
   const int last_k = h.tw >= 0 ? h.tw : k_last;
   R->levels.clear();
-  for (int j = 0; j <= h.last; ++j) R->levels.push_back({h.level_off[j], h.level_cnt[j]});
+  for (int j = 0; j <= h.last; ++j) R->levels.push_back({hl->level_off[j], hl->level_cnt[j]});
   R->yes = h.tw >= 0 ? 1 : 0;
   R->states_expanded = h.states_expanded;
   R->candidates = h.candidates;
@@ -1069,15 +1184,15 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
     R->expand_seconds = (double)ms * 1e-3;
   }
   unsigned long long out_states = 0;
-  for (int j = 1; j <= h.last; ++j) out_states += h.level_cnt[j];
+  for (int j = 1; j <= h.last; ++j) out_states += hl->level_cnt[j];
   R->expand_bytes = (double)(h.states_expanded + h.generated + 2ull * out_states) * (double)w + (double)out_states;
   R->fp_sum.assign(1, 0ull);
   R->fp_xor.assign(1, 0ull);
   if (c->cfg.fingerprints) {
     for (int j = 1; j <= h.last; ++j) {
       TW_CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(LevelCounters), c->stream));
-      TW_LAUNCH(c, launch_fingerprint(kc, static_cast<char*>(f.keys) + h.level_off[j] * w, h.level_cnt[j], c->d_ctr,
-                                      c->stream));
+      TW_LAUNCH(c, launch_fingerprint(kc, static_cast<char*>(f.keys[grp]) + hl->level_off[j] * w, hl->level_cnt[j],
+                                      c->d_ctr, c->stream));
       TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
       TW_CK(cudaStreamSynchronize(c->stream));
       R->fp_sum.push_back(c->h_ctr->fp_sum);
@@ -1224,21 +1339,30 @@ int level_keys_graph(tw_ctx* c, const HostGraph& g, int k, int level, uint64_t* 
     if (keys == nullptr) return TW_ERR_INVALID;
     const LevelRec& lr = R.levels[level];
     const size_t w = key_bytes(kc);
-    const char* src = lr.hkeys ? lr.hkeys : static_cast<const char*>(c->keys.ptr) + lr.off * w;
-    if (kc == kKey32) {
-      // 32-bit states widen to the ABI's 64-bit words: by a kernel into a
-      // device buffer of the caller, or on the host side of the copy
-      if (is_device_ptr(keys)) {
-        TW_LAUNCH(c, launch_widen32(reinterpret_cast<const uint32_t*>(src), reinterpret_cast<unsigned long long*>(keys),
-                                    cnt, c->stream));
-      } else {
-        std::vector<uint32_t> narrow((size_t)cnt);
-        TW_CK(cudaMemcpyAsync(narrow.data(), src, (size_t)cnt * 4, cudaMemcpyDefault, c->stream));
-        TW_CK(cudaStreamSynchronize(c->stream));
-        for (unsigned long long x = 0; x < cnt; ++x) keys[x] = narrow[x];
+    // the level's keys: one run, or (an out-of-core level split between
+    // device and host memory) a device run followed by a host run
+    const char* src[2] = {lr.hkeys ? lr.hkeys : static_cast<const char*>(c->keys.ptr) + lr.off * w, lr.htail};
+    const unsigned long long run[2] = {cnt - lr.tail, lr.tail};
+    const bool dev_out = is_device_ptr(keys);
+    unsigned long long at = 0;
+    for (int p = 0; p < 2; ++p) {
+      if (run[p] == 0) continue;
+      if (kc == kKey32) {
+        // 32-bit states widen to the ABI's 64-bit words: by a kernel into a
+        // device buffer of the caller, or on the host side of the copy
+        if (dev_out) {
+          TW_LAUNCH(c, launch_widen32(reinterpret_cast<const uint32_t*>(src[p]),
+                                      reinterpret_cast<unsigned long long*>(keys) + at, run[p], c->stream));
+        } else {
+          std::vector<uint32_t> narrow((size_t)run[p]);
+          TW_CK(cudaMemcpyAsync(narrow.data(), src[p], (size_t)run[p] * 4, cudaMemcpyDefault, c->stream));
+          TW_CK(cudaStreamSynchronize(c->stream));
+          for (unsigned long long x = 0; x < run[p]; ++x) keys[at + x] = narrow[x];
+        }
+      } else if ((rc = put_from_device(c, keys + at * (size_t)g.words, src[p], (size_t)run[p] * (size_t)g.words * 8))) {
+        return rc;
       }
-    } else if ((rc = put_from_device(c, keys, src, (size_t)cnt * (size_t)g.words * 8))) {
-      return rc;
+      at += run[p];
     }
   }
   TW_CK(cudaStreamSynchronize(c->stream));

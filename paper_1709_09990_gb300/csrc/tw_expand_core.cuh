@@ -515,6 +515,8 @@ struct ExpandParams {
   int mmw;    // 1: minor-min-width pruning of the states before they are extended
   unsigned long long ranges;  // ranged kernels: the hash space is split in this many ranges,
   unsigned long long range;   // and only pairs of this one are inserted (the table is its slice)
+  unsigned int group_block = 0, group_blocks = 0;  // a level expanded by a group of a grid's
+                                                   // blocks: this block's index in it and its size
 };
 
 // One level i -> i+1 by the whole block: the adjacency rows go to shared
@@ -540,8 +542,10 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   const K valid = kfirst_n<K>(p.n);
   unsigned long long generated_total = 0;
   const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
-  const unsigned long long first = kBlockLocal ? (unsigned long long)warp : (unsigned long long)blockIdx.x * kWarps + warp;
-  const unsigned long long stride = kBlockLocal ? (unsigned long long)kWarps : (unsigned long long)gridDim.x * kWarps;
+  const unsigned long long blk = p.group_blocks ? p.group_block : blockIdx.x;
+  const unsigned long long nblk = p.group_blocks ? p.group_blocks : gridDim.x;
+  const unsigned long long first = kBlockLocal ? (unsigned long long)warp : blk * kWarps + warp;
+  const unsigned long long stride = kBlockLocal ? (unsigned long long)kWarps : nblk * kWarps;
   LevelOut<K, false> out;
   out.keys = p.out_keys;
   out.pred = p.out_pred;

@@ -96,9 +96,11 @@ struct tw_ctx {
   // out-of-core decide runs: two pinned, device-mapped host buffers that hold
   // the levels that do not fit the device (reused from run to run)
   HostChunk ooc_host[2] = {{nullptr, nullptr, 0}, {nullptr, nullptr, 0}};
+  LevelCounters* d_ctr_host = nullptr;  // counters of the passes that write to host memory
   // fused small solves: state, two tables and the level arena in one buffer,
   // a pinned mirror of the state, and the graphs whose fused run gave up
   DevBuf fused;
+  bool fused_clean = false;  // every table slot of the fused buffer is empty
   FusedState* h_fused = nullptr;
   std::vector<unsigned long long> fused_skip;
   // options of Section 3.1 for the decide run being prepared
@@ -152,6 +154,8 @@ struct LevelRec {
   unsigned long long off = 0;
   unsigned long long count = 0;
   const char* hkeys = nullptr;     // host copy (spill_levels), else in c->keys at off
+  const char* htail = nullptr;     // out of core: the last `tail` keys, in host memory
+  unsigned long long tail = 0;
   const uint8_t* hpred = nullptr;  // host copy of the predecessors, else in c->pred
 };
 

@@ -147,16 +147,25 @@ cudaError_t launch_graph_clear(KeyClass kc, const GraphState* st, void* table, c
 cudaError_t launch_graph_expand(const GraphState* st, const ExpandLaunch& base, cudaStream_t s);
 
 // ---- fused small solve (tw_fused.cu) -----------------------------------------
-// Device state of a fused solve (zeroed by the host before the launch).
+constexpr int kFusedMaxGroups = 4;  // decide runs of the sweep in flight at once
+
+// Device state of one group of a fused solve (zeroed by the host before the
+// launch).  Group 0's state also holds the solve's summary and the window
+// barrier of the whole grid.
 struct FusedState {
-  unsigned long long level_off[130];  // arena index of level j of the final run
+  unsigned long long level_off[130];  // arena index of level j of the group's run
   unsigned long long level_cnt[130];  // |L_j|
   LevelCounters ctr[130];             // counters of the expansion that built level j
-  unsigned long long states_expanded, candidates, generated;  // over every decide run
-  unsigned int arrive, gen, error;    // grid barrier; error: a barrier wait gave up
-  int status;                         // 1: finished, 2: gave up at k = last (the host goes on)
-  int tw, last;                       // the first yes k (-1: none up to k_last) and the
-                                      // index of the final level of the last run
+  unsigned long long states_expanded, candidates, generated;  // group 0: over the counted runs
+  unsigned long long run_states, run_candidates, run_generated;  // the group's current run
+  unsigned int arrive, gen, error;    // the group's barrier; error (group 0): a wait gave up
+  unsigned int w_arrive, w_gen;       // group 0: barrier of all blocks at the end of a window
+  int result, run_last;               // the group's run: 0 no, 1 yes, 2 gave up, -1 not run;
+                                      // index of its final level
+  int status;                         // group 0: 1 finished, 2 gave up at k = last
+  int tw, last, group;                // group 0: the first yes k (-1: none up to k_last), the
+                                      // index of the final level of the deciding run and
+                                      // the group that ran it
 };
 
 struct FusedLaunch {
@@ -164,13 +173,15 @@ struct FusedLaunch {
   const void* adj;                    // n rows in the state layout
   const unsigned long long* adj64;    // n rows of words64 words
   int n, words64, k0, k_last, max_probes, load_pct;  // decide runs at k0 .. k_last
-  void* keys;                         // arena of arena_cap states
-  uint8_t* pred;
+  int groups;                         // runs in flight at once: k, k+1, .. (1 .. kFusedMaxGroups)
+  int tables_clean;                   // 1: every table slot is empty (the last launch emptied them)
+  void* keys[kFusedMaxGroups];        // per group: arena of arena_cap states
+  uint8_t* pred[kFusedMaxGroups];
   unsigned long long arena_cap;
-  void* table0;
-  void* table1;
+  void* table0[kFusedMaxGroups];      // per group: two tables of table_cap slots
+  void* table1[kFusedMaxGroups];
   unsigned long long table_cap;       // slots of each table
-  FusedState* st;
+  FusedState* st[kFusedMaxGroups];
   int32_t* order;
   int32_t* parent;
   unsigned long long* bags;

@@ -38,7 +38,7 @@ class Config(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("partition_table_mb", ctypes.c_int), ("mmw_prune", ctypes.c_int),
                 ("spill_levels", ctypes.c_int), ("out_of_core", ctypes.c_int),
                 ("fused_states", ctypes.c_int), ("batch_kernel", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("host_cap_mb", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -145,7 +145,8 @@ class Context:
                  ub_shortcut: bool = False, time_kernels: bool = False, graph_levels: int = 0,
                  autotune: bool = False, clique_skip: bool = False, disjoint_paths: bool = False,
                  partition_table_mb: int = 0, mmw_prune: bool = False, spill_levels: bool = False,
-                 out_of_core: bool = False, fused_states: int = 0, batch_kernel: int = 0):
+                 out_of_core: bool = False, fused_states: int = 0, batch_kernel: int = 0,
+                 host_cap_mb: int = 0):
         cfg = Config()
         cfg.device = device
         cfg.fingerprints = int(fingerprints)
@@ -166,6 +167,7 @@ class Context:
         cfg.out_of_core = int(out_of_core)
         cfg.fused_states = int(fused_states)
         cfg.batch_kernel = int(batch_kernel)
+        cfg.host_cap_mb = int(host_cap_mb)
         h = _vp()
         _check(lib().tw_create(ctypes.byref(h), ctypes.byref(cfg)), "tw_create")
         self._h = h

@@ -30,3 +30,15 @@ def assert_decide_matches(ctx, adj, k, check_order=True):
         assert oracle.width_q(adj, order) <= k
         assert oracle.width_elim(adj, order) <= k
     return got, exp
+
+
+def fingerprint_sums(keys: np.ndarray):
+    """Sum (mod 2^64) and xor of the splitmix64 output function over 64-bit
+    keys: the level digest the libtw counters and the oracle report."""
+    z = keys.astype(np.uint64).reshape(-1)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+        s = int(np.sum(z, dtype=np.uint64))
+    return s, int(np.bitwise_xor.reduce(z)) if z.size else 0

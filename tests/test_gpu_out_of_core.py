@@ -7,7 +7,9 @@ use caps far below what the in-memory run needs and must give the same level
 sets: the full decide(6) of the n = 40 benchmark graph (golden record,
 79,399,414 states) under a 48 MB cap, and the first eleven levels of the
 partial 10-tree n = 60 at k = 10 (level 10: 566,907,942 states, 4.5 GB of
-keys) under a 1 GB cap.
+keys) under a 1 GB cap.  With a host limit as well (host_cap_mb), the peak
+levels of the n = 40 graph fit neither memory alone and are split between
+device and host memory.
 """
 import json
 import os
@@ -17,7 +19,7 @@ import pytest
 
 import oracle
 from paper_1709_09990_gb300 import graphgen as gg
-from tests.gpu_util import context
+from tests.gpu_util import context, fingerprint_sums
 
 pytestmark = pytest.mark.gpu
 
@@ -66,3 +68,43 @@ def test_out_of_core_level_keys_match_the_oracle():
     with context(mem_cap_bytes=1 << 16, out_of_core=True) as ctx:
         r = ctx.decide_level(adj, k=8, level=6)
     assert np.array_equal(oracle.sort_keys(r["keys"]), exp)
+
+
+# decide(6) of the n = 40 graph with 64 MB of device memory and 48 MB of host
+# memory: levels 20 and 21 (46.9 MB and 45.8 MB of keys) fit neither memory
+# alone next to each other, so at least one of them is split into a device
+# part and a host part.
+SPLIT_CAPS = dict(mem_cap_bytes=64 << 20, host_cap_mb=48, out_of_core=True)
+
+
+def test_levels_split_between_device_and_host_match_the_golden_record():
+    rec = json.load(open(os.path.join(GOLDEN, "rgg40_seed0_k6.json")))["decide"][0]
+    adj = gg.workload_rgg40()
+    with context(fingerprints=True, **SPLIT_CAPS) as ctx:
+        r = ctx.decide(adj, k=6)
+        st = r["stats"]
+        assert r["yes"]
+        assert st["level_size"] == rec["level_size"]
+        assert st["fp_sum"] == [int(x) for x in rec["fp_sum"]]
+        assert st["fp_xor"] == [int(x) for x in rec["fp_xor"]]
+        assert st["generated"] == rec["canonical"]
+        assert st["peak_frontier_bytes"] <= 64 << 20
+    # the same device cap with too little host memory for the split is a
+    # capacity error, not a wrong answer
+    with context(mem_cap_bytes=64 << 20, host_cap_mb=8, out_of_core=True) as ctx:
+        assert ctx.decide(adj, k=6, raise_on_error=False)["status"] == 2
+
+
+@pytest.mark.parametrize("level", [20, 21])
+def test_split_level_downloads_whole(level):
+    # the peak levels downloaded set by set: the device part and the host part
+    # together hold each set of the level once (size and digest of the
+    # oracle's golden record)
+    rec = json.load(open(os.path.join(GOLDEN, "rgg40_seed0_k6.json")))["decide"][0]
+    adj = gg.workload_rgg40()
+    with context(**SPLIT_CAPS) as ctx:
+        r = ctx.decide_level(adj, k=6, level=level)
+    keys = r["keys"].reshape(-1)
+    assert r["count"] == rec["level_size"][level] == keys.size
+    assert np.unique(keys).size == keys.size
+    assert fingerprint_sums(keys) == (int(rec["fp_sum"][level]), int(rec["fp_xor"][level]))
