@@ -53,13 +53,16 @@ def parse():
                          "10-tree n=60 at k=10; batch: the 4096-graph batch vs a per-graph loop; learned: the "
                          "learned starting bound vs the plain sweep")
     ap.add_argument("--graphs", type=int, default=0, help="batch/learned: number of graphs (0 = full workload)")
+    ap.add_argument("--triage-cap-gb", type=float, default=0.5,
+                    help="batch/learned: device cap of the per-graph loop that sorts out the heavy graphs")
+    ap.add_argument("--heavy", action="store_true", help="batch: also solve the heavy graphs (default cap)")
     ap.add_argument("--mem-cap-gb", type=float, default=0.0, help="device memory cap per context (0 = default)")
     ap.add_argument("--spill-levels", action="store_true",
                     help="keep finished levels in pinned host memory (tw_config.spill_levels)")
     ap.add_argument("--no-sub", action="store_true", help="skip the other workloads' sub-records")
     ap.add_argument("--in-core", action="store_true", help="pktree60: no out-of-core levels (stop at the cap)")
     ap.add_argument("--host-cap-gb", type=float, default=0.0,
-                    help="pktree60: pinned host memory for out-of-core levels (0 = 85%% of the memory this "
+                    help="pktree60: pinned host memory for out-of-core levels (0 = 80%% of the memory this "
                          "process may use: MemAvailable, or the cgroup limit when lower)")
     ap.add_argument("--plain", action="store_true", help="pktree60: without the clique skip")
     ap.add_argument("--partition-mb", type=int, default=0,
@@ -344,6 +347,20 @@ def sub_pktree60(args):
     return out
 
 
+def sub_batch(args, count=512):
+    """The first `count` graphs of the 4096-graph batch workload: the light
+    ones (solved by the per-graph loop within 2^21 states under the triage
+    cap) through the persistent batched kernel, the level-synchronous one and
+    the per-graph loop."""
+    from paper_1709_09990_gb300 import graphgen as gg
+    graphs = gg.batch_graphs(count)
+    light, loop_tw, _, loop_secs = batch_light(graphs, int(args.triage_cap_gb * (1 << 30)))
+    rec = batch_arms(graphs, light, loop_tw, loop_secs)
+    return {"workload": f"the first {count} graphs of the 4096-graph batch workload (seeds 0..{count - 1}), the "
+                        f"light ones (solved within {LIGHT_STATES} states)", "dtype": "u32/u64",
+            "heavy_graphs": count - len(light), **rec}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -442,9 +459,10 @@ def run_ours(args):
            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
            "roofline": roofline, "clocks": clocks}
     if world == 1 and not args.no_sub:
-        # the other single-graph workloads, after the timed region
+        # the other workloads, after the timed region
         out["other_workloads"] = {"gnp20": sub_gnp20(stream, max(5, args.steps)),
-                                  "pktree60": sub_pktree60(args)}
+                                  "pktree60": sub_pktree60(args),
+                                  "batch": sub_batch(args)}
     ctx.close()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
@@ -530,7 +548,7 @@ def run_gnp20(args):
 
 def host_cap_mb(args) -> int:
     """Pinned host memory (MB) the out-of-core levels may take: --host-cap-gb,
-    else 85% of what this process may use (MemAvailable, or the cgroup's
+    else 80% of what this process may use (MemAvailable, or the cgroup's
     memory limit minus its current use when that is lower)."""
     if args.host_cap_gb:
         return int(args.host_cap_gb * 1024)
@@ -550,7 +568,7 @@ def host_cap_mb(args) -> int:
                 avail = room if avail is None else min(avail, room)
         except (OSError, ValueError):
             pass
-    return int(0.85 * avail) >> 20 if avail else 0
+    return int(0.80 * avail) >> 20 if avail else 0
 
 
 def run_pktree60(args):
@@ -591,64 +609,99 @@ def run_pktree60(args):
            if st["expand_seconds"] else None})
 
 
-def run_batch(args):
-    """The 4096-graph batch (G(n,p) and partial k-trees, n in [16, 48]): the
-    persistent batched kernel (one launch for the batch), the level-synchronous
-    batched kernel and a per-graph tw_solve loop on the same GPU.  Graphs are
-    split by the loop's states per solve: the light ones stay in a block's
-    workspace of the persistent kernel, the heavy ones leave the batch for the
-    single-graph path in every arm; both shares are reported."""
-    import numpy as np
-    from paper_1709_09990_gb300 import graphgen as gg
+def triage_loop(graphs, cap_bytes):
+    """The plain per-graph loop (tw_solve with ordering) under a small device
+    cap: graphs whose sweep fits it solve exactly as under any larger cap (the
+    same fused launch or level loop), the others stop at the cap quickly with
+    TW_ERR_CAPACITY.  Returns per-graph tw (-1 over the cap), states and
+    seconds."""
     from paper_1709_09990_gb300 import native
-    N = args.graphs or 4096
-    graphs = gg.batch_graphs(N)
-    cap = int(args.mem_cap_gb * (1 << 30)) if args.mem_cap_gb else 0
-    out = {}
-    with native.Context(device=0, mem_cap_bytes=cap) as ctx, \
-            native.Context(device=0, mem_cap_bytes=cap, batch_kernel=1) as sync:
-        ctx.solve_batch(graphs[:64])
-        sync.solve_batch(graphs[:64])
-        loop_tw, loop_states, loop_t = [], [], []
+    tw, states, secs = [], [], []
+    with native.Context(device=0, mem_cap_bytes=cap_bytes) as ctx:
+        for a in graphs[:16]:
+            try:
+                ctx.solve(a, want_order=True)
+            except native.TwError:
+                pass
         for a in graphs:
             t = time.perf_counter()
             try:
                 r = ctx.solve(a, want_order=True)
-                loop_tw.append(r["tw"])
-                loop_states.append(r["stats"]["states_expanded"])
+                tw.append(r["tw"])
+                states.append(r["stats"]["states_expanded"])
             except native.TwError:
-                loop_tw.append(-1)
-                loop_states.append(-1)
-            loop_t.append(time.perf_counter() - t)
-        light = [i for i in range(N) if 0 <= loop_states[i] <= LIGHT_STATES]
-        heavy = [i for i in range(N) if i not in set(light)]
-        for name, sel in (("light", light), ("heavy", heavy), ("all", list(range(N)))):
-            sub = [graphs[i] for i in sel]
-            rec = {"graphs": len(sel), "loop_seconds": round(sum(loop_t[i] for i in sel), 3)}
-            for arm, c in (("persistent", ctx), ("level_synchronous", sync)):
-                if arm == "level_synchronous" and name == "all":
-                    continue
-                t = time.perf_counter()
-                res = c.solve_batch(sub)
-                dt = time.perf_counter() - t
-                ok = res["per_graph_status"] == 0
-                rec[arm] = {"seconds": round(dt, 3), "solved": int(ok.sum()),
-                            "same_answers_as_loop": bool(all(int(res["tw"][j]) == loop_tw[i]
-                                                             for j, i in enumerate(sel) if ok[j])),
-                            "kernel_launches": res["stats"]["kernel_launches"],
-                            "states_per_s": round(res["stats"]["states_expanded"] / dt, 1) if dt else None}
-            rec["loop_kernel_launches_note"] = "per-graph tw_solve: bounds + one fused launch, or the level loop"
-            if rec["persistent"]["seconds"]:
-                rec["persistent_speedup_vs_loop"] = round(rec["loop_seconds"] / rec["persistent"]["seconds"], 3)
-            out[name] = rec
-    total_loop = sum(loop_t)
-    _line("time to exact tw, batch", out["all"]["persistent"]["seconds"], "s", args,
+                tw.append(-1)
+                states.append(-1)
+            secs.append(time.perf_counter() - t)
+    return tw, states, secs
+
+
+def batch_light(graphs, triage_cap, light_states=None):
+    """Light graphs of a set (the per-graph loop solves them under the triage
+    cap within light_states states): their indices, loop answers and loop
+    time, and the number of heavy graphs."""
+    light_states = light_states or LIGHT_STATES
+    tw, states, secs = triage_loop(graphs, triage_cap)
+    light = [i for i in range(len(graphs)) if tw[i] >= 0 and states[i] <= light_states]
+    return light, tw, states, secs
+
+
+def batch_arms(graphs, light, loop_tw, loop_secs):
+    """The persistent batched kernel (one launch for all light graphs) and the
+    level-synchronous batched kernel on the light graphs, against the loop's
+    time on the same graphs; default device cap."""
+    from paper_1709_09990_gb300 import native
+    sub = [graphs[i] for i in light]
+    rec = {"graphs": len(sub), "loop_seconds": round(sum(loop_secs[i] for i in light), 4)}
+    with native.Context(device=0) as ctx, native.Context(device=0, batch_kernel=1) as sync:
+        ctx.solve_batch(sub[:64])
+        sync.solve_batch(sub[:64])
+        for arm, c in (("persistent", ctx), ("level_synchronous", sync)):
+            t = time.perf_counter()
+            res = c.solve_batch(sub)
+            dt = time.perf_counter() - t
+            ok = res["per_graph_status"] == 0
+            rec[arm] = {"seconds": round(dt, 4), "solved": int(ok.sum()),
+                        "same_answers_as_loop": bool(all(int(res["tw"][j]) == loop_tw[i]
+                                                         for j, i in enumerate(light) if ok[j])),
+                        "kernel_launches": res["stats"]["kernel_launches"],
+                        "states_per_s": round(res["stats"]["states_expanded"] / dt, 1) if dt else None,
+                        "speedup_vs_loop": round(rec["loop_seconds"] / dt, 3) if dt else None}
+    return rec
+
+
+def run_batch(args):
+    """The 4096-graph batch (G(n,p) and partial k-trees, n in [16, 48]).
+    Graphs are first sorted by the per-graph loop (tw_solve with ordering)
+    under a small device cap (--triage-cap-gb): the light ones (solved within
+    2^21 states) are the ones the batch design is for; on them the persistent
+    batched kernel (one launch) and the level-synchronous batched kernel run
+    against the loop's time.  Heavy graphs leave the batch for the
+    single-graph path in every arm, so they measure that path, not the batch;
+    they are counted, and solved here only with --heavy (default cap)."""
+    from paper_1709_09990_gb300 import graphgen as gg
+    from paper_1709_09990_gb300 import native
+    N = args.graphs or 4096
+    graphs = gg.batch_graphs(N)
+    t = time.perf_counter()
+    light, loop_tw, loop_states, loop_secs = batch_light(graphs, int(args.triage_cap_gb * (1 << 30)))
+    triage_s = time.perf_counter() - t
+    rec = batch_arms(graphs, light, loop_tw, loop_secs)
+    heavy = [i for i in range(N) if i not in set(light)]
+    out = {"light": rec, "heavy_graphs": len(heavy),
+           "heavy_over_triage_cap": sum(1 for i in heavy if loop_tw[i] < 0),
+           "triage_seconds": round(triage_s, 3)}
+    if args.heavy:
+        with native.Context(device=0) as ctx:
+            t = time.perf_counter()
+            res = ctx.solve_batch([graphs[i] for i in heavy])
+            out["heavy"] = {"seconds": round(time.perf_counter() - t, 3),
+                            "solved": int((res["per_graph_status"] == 0).sum())}
+    _line("time to exact tw, batch (light graphs)", rec["persistent"]["seconds"], "s", args,
           {"workload": f"{N} seeded graphs: even seeds G(n,p), n~U{{16..48}}, p~U[0.1,0.5]; odd seeds partial "
                        "k-trees, k~U{3..12}, 30% edges removed", "graphs": N,
-           "mem_cap_gb": round(cap / (1 << 30), 1) if cap else "default (150 GB or 90% of free memory)",
-           "light_states_limit": LIGHT_STATES},
-          {"loop_seconds": round(total_loop, 3), "split": out,
-           "solved": out["all"]["persistent"]["solved"]})
+           "light_states_limit": LIGHT_STATES, "triage_cap_gb": args.triage_cap_gb},
+          out)
 
 
 LIGHT_STATES = 1 << 21  # states per solve below which a graph counts as light in the batch report
@@ -657,19 +710,29 @@ LIGHT_STATES = 1 << 21  # states per solve below which a graph counts as light i
 def run_learned(args):
     """Learned starting bound: label and train on the 20000 training graphs
     (n in [12, 40]), then solve the 2000 held-out graphs (n in [30, 56]) with
-    proposals (batched) and with the plain per-graph sweep."""
+    proposals (batched) and with the plain per-graph sweep.  Labels come from
+    the batched solve under the triage cap (graphs over it are left out of
+    training); the held-out graphs are sorted by the per-graph loop under the
+    same cap, and the arms are compared on the ones it solves (default cap for
+    the batched arms)."""
     import numpy as np
     from paper_1709_09990_gb300 import graphgen as gg
     from paper_1709_09990_gb300 import learned
     from paper_1709_09990_gb300 import native
     ntr = args.graphs * 10 if args.graphs else 20000
     nte = args.graphs or 2000
-    cap = int(args.mem_cap_gb * (1 << 30)) if args.mem_cap_gb else 0
+    tcap = int(args.triage_cap_gb * (1 << 30))
     tr = [gg.mixed_graph(10**6 + j, 12, 40, j % 2 == 0) for j in range(ntr)]
     te = [gg.mixed_graph(2 * 10**6 + j, 30, 56, j % 2 == 0) for j in range(nte)]
-    with native.Context(device=0, mem_cap_bytes=cap, spill_levels=args.spill_levels) as ctx:
-        L = learned.label(ctx, tr)
-        ok = L["status"] == 0
+    with native.Context(device=0, mem_cap_bytes=tcap) as small:
+        L = learned.label(small, tr)
+    ok = L["status"] == 0
+    t = time.perf_counter()
+    loop_tw, loop_states, loop_secs = triage_loop(te, tcap)
+    loop_all_s = time.perf_counter() - t
+    solved = [i for i in range(nte) if loop_tw[i] >= 0]
+    sub = [te[i] for i in solved]
+    with native.Context(device=0) as ctx:
         # offset chosen on a validation split of the training graphs
         idx = np.arange(len(tr))[ok]
         val = idx[idx % 10 == 0]
@@ -680,39 +743,32 @@ def run_learned(args):
         lbv = np.array([max(ctx.bounds(tr[i])[:2]) for i in val])
         pv = learned.propose(ctx, T["params"], L["x"][val], L["n"][val])
         off = learned.choose_offset(pv, L["tw"][val], lbv)
-        n = np.array([len(g) for g in te], np.int32)
+        n = np.array([len(g) for g in sub], np.int32)
+        ctx.solve_batch(sub[:32])
         t = time.perf_counter()
-        hint = learned.propose(ctx, T["params"], ctx.features(te), n, off)
-        lk = ctx.solve_batch(te, k_hint=hint)
+        hint = learned.propose(ctx, T["params"], ctx.features(sub), n, off)
+        lk = ctx.solve_batch(sub, k_hint=hint)
         t_learned = time.perf_counter() - t
         t = time.perf_counter()
-        pb = ctx.solve_batch(te)
+        pb = ctx.solve_batch(sub)
         t_plain_batch = time.perf_counter() - t
-        loop_tw, runs = [], 0
-        t = time.perf_counter()
-        for g in te:
-            try:
-                r = ctx.solve(g, want_order=True)
-                loop_tw.append(r["tw"])
-                runs += r["stats"]["decide_runs"]
-            except native.TwError:
-                loop_tw.append(-1)
-        t_loop = time.perf_counter() - t
     okl = lk["per_graph_status"] == 0
-    loop_tw = np.array(loop_tw)
-    both = okl & (loop_tw >= 0)
+    ref = np.array([loop_tw[i] for i in solved])
+    t_loop = sum(loop_secs[i] for i in solved)
     _line("time to exact tw, learned-k batched", round(t_learned, 3), "s", args,
           {"workload": f"train {ntr} graphs n in [12,40] (seeds 1e6+j), test {nte} graphs n in [30,56] "
-                       "(seeds 2e6+j), mixed G(n,p) / partial k-trees",
-           "mem_cap_gb": round(cap / (1 << 30), 1) if cap else "default (150 GB or 90% of free memory)"},
+                       "(seeds 2e6+j), mixed G(n,p) / partial k-trees", "triage_cap_gb": args.triage_cap_gb},
           {"label_seconds": round(L["seconds"], 2), "train_seconds": round(train_s, 3),
            "train_graphs_used": int(ok.sum()), "final_train_loss": float(T["loss"][-1]), "offset": off,
-           "test_solved": int(okl.sum()), "test_capacity": int((lk["per_graph_status"] == 2).sum()),
-           "exact_answer_rate": float((lk["tw"][both] == loop_tw[both]).mean()) if both.any() else None,
-           "proposal_hits_tw": float((np.rint(hint[both]) == loop_tw[both]).mean()) if both.any() else None,
+           "test_graphs_compared": len(solved), "test_over_triage_cap": nte - len(solved),
+           "test_solved_learned": int(okl.sum()),
+           "exact_answer_rate": float((lk["tw"][okl] == ref[okl]).mean()) if okl.any() else None,
+           "plain_batch_same_answers": bool((pb["tw"] == ref).all()),
+           "proposal_hits_tw": float((np.rint(hint) == ref).mean()) if len(ref) else None,
            "plain_loop_seconds": round(t_loop, 3), "plain_batch_seconds": round(t_plain_batch, 3),
-           "speedup_vs_plain_loop": round(t_loop / t_learned, 3),
-           "decide_runs": {"learned_batch": lk["stats"]["decide_runs"], "plain_loop": runs}})
+           "speedup_vs_plain_loop": round(t_loop / t_learned, 3) if t_learned else None,
+           "loop_seconds_with_triaged_out_graphs": round(loop_all_s, 3),
+           "decide_runs": {"learned_batch": lk["stats"]["decide_runs"], "plain_batch": pb["stats"]["decide_runs"]}})
 
 
 def main():

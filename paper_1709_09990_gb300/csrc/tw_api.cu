@@ -132,7 +132,6 @@ void tw_destroy(tw_ctx* c) {
   for (const tw_ctx::HostChunk& ch : c->ooc_host)
     if (ch.ptr) cudaFreeHost(ch.ptr);
   if (c->d_ctr) cudaFree(c->d_ctr);
-  if (c->d_ctr_host) cudaFree(c->d_ctr_host);
   if (c->h_ctr) cudaFreeHost(c->h_ctr);
   if (c->h_fused) cudaFreeHost(c->h_fused);
   for (auto& e : c->graphs) {

@@ -699,17 +699,26 @@ int run_batch_persistent(tw_ctx* c, const std::vector<HostGraph>& graphs, const 
   return TW_OK;
 }
 
-// Graphs with n <= 64 go through the batched kernel; graphs it evicts and
-// graphs with n > 64 are solved one at a time by the single-graph path.
+// Graphs with n <= 64 go through the batched kernels: the persistent one
+// first (by default), then the level-synchronous one for the graphs that
+// outgrew a block's workspace (it holds levels of up to 2^21 sets per graph);
+// graphs it evicts in turn and graphs with n > 64 are solved one at a time by
+// the single-graph path.
 int solve_batch_gpu(tw_ctx* c, const std::vector<HostGraph>& graphs, const std::vector<int>& idx,
                     const std::vector<float>* hint, const std::vector<int64_t>& order_off, int* htw,
                     std::vector<int32_t>* hord, std::vector<int>* hst, tw_stats* st) {
   NvtxRange range("tw solve_batch graphs=%d", (int)idx.size());
   std::vector<int> small, single;
   for (int i : idx) (graphs[i].n <= 64 ? small : single).push_back(i);
-  int rc = c->cfg.batch_kernel == 1 ? run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single, nullptr)
-                                    : run_batch_persistent(c, graphs, small, hint, order_off, htw, hord, hst, st, &single,
-                                                           nullptr, 0);
+  int rc;
+  if (c->cfg.batch_kernel == 1) {
+    rc = run_batch(c, graphs, small, hint, order_off, htw, hord, hst, st, &single, nullptr);
+  } else {
+    std::vector<int> outgrown;
+    rc = run_batch_persistent(c, graphs, small, hint, order_off, htw, hord, hst, st, &outgrown, nullptr, 0);
+    if (rc == TW_OK && !outgrown.empty())
+      rc = run_batch(c, graphs, outgrown, hint, order_off, htw, hord, hst, st, &single, nullptr);
+  }
   if (rc) return rc;
   for (int gi : single) {
     const HostGraph& hg = graphs[gi];

@@ -29,12 +29,6 @@ using core::ExpandParams;
 using K = unsigned long long;
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ double binom_b(int n, int r) {
-  if (r < 0 || r > n) return 0.0;
-  double b = 1.0;
-  for (int i = 1; i <= r; ++i) b = b * (double)(n - r + i) / (double)i;
-  return b;
-}
 
 // The block's view of its workspace.
 struct Work {
@@ -107,18 +101,11 @@ __device__ __noinline__ bool block_decide(const BatchSolveArgs& a, const K* adj,
   }
   unsigned long long off = 0, cnt = 1, prev_cnt = 0;
   for (int i = 0; i <= n - k - 2; ++i) {
-    const double bound = fmin((double)cnt * (double)(n - i), binom_b(n, i + 1)) + 1.0;
-    double est = (double)n;
-    if (i > 0) {
-      double r = prev_cnt > 0 ? (double)cnt / (double)prev_cnt : 1.0;
-      r = fmin(fmax(r, 0.25), (double)(n - i));
-      est = (double)cnt * r;
-    }
-    const double table_est = fmin(est * 1.25 + 1024.0, bound);
-    unsigned long long slots = (unsigned long long)ceil(table_est * 100.0 / (double)a.load_pct);
-    if (slots < 64ull) slots = 64ull;
+    // the plan of the level in integer arithmetic (FP64 is slow on this part)
+    unsigned long long table_est = 0, slots = 0;
+    core::plan_level(cnt, prev_cnt, n, i, a.load_pct, &table_est, &slots);
     const unsigned long long out_off = off + cnt;
-    if (out_off >= a.A || (double)(a.A - out_off) < fmin(table_est, bound)) return false;
+    if (out_off >= a.A || a.A - out_off < table_est) return false;
     if (slots > a.T) slots = a.T;
     const int t = i & 1;
     unsigned long long got = 0, gen = 0;

@@ -225,9 +225,7 @@ int run_decide_ooc(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, int st
   release(c, &c->pred);
   release(c, &c->cand_key);
   release(c, &c->cand_v);
-  if (!c->d_ctr_host) TW_CK(cudaMalloc(reinterpret_cast<void**>(&c->d_ctr_host), sizeof(LevelCounters)));
   DevBuf* dev[2] = {&c->keys, &c->ooc_keys};
-  LevelCounters* d_ctr[2] = {c->d_ctr, c->d_ctr_host};  // [0]: device part, [1]: host part
   const int load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 75;
   const int max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
   const size_t margin = std::min<size_t>(64ull << 20, c->mem_cap / 16);
@@ -313,93 +311,78 @@ int run_decide_ooc(tw_ctx* c, KeyClass kc, int n, int k, DecideResult* R, int st
         slice_bytes = (size_t)((slice_slots * w + 15) & ~15ull);
         if (alloc_exact(c, &c->table, slice_bytes)) break;
       }
-      // both counter blocks start at zero; the host keeps their values after
-      // every pass so that a pass can be redone from them
-      TW_CK(cudaMemsetAsync(c->d_ctr_host, 0, sizeof(LevelCounters), c->stream));
+      // the passes append to one list that fills the device part first and
+      // goes on in the host part (the ranged kernel's split output)
+      char* out_first = cap_part[0] ? out_part[0] : out_part[1];
+      char* out_tail = cap_part[0] && cap_part[1] ? out_part[1] : nullptr;
       TW_CK(cudaMemsetAsync(c->d_ctr, 0, sizeof(LevelCounters), c->stream));
-      LevelCounters done[2] = {LevelCounters{}, LevelCounters{}};
+      LevelCounters h{};
       bool replan = false;
       ms_total = 0.f;
       launches = 0;
-      for (unsigned long long r = 0; r < P && !replan; ++r) {
-        // the part this pass writes to: the host part while it has room for
-        // a pass of the size seen so far, else the device part
-        const unsigned long long so_far = done[0].out_count + done[1].out_count;
-        const double expect = (r > 0 ? (double)so_far / (double)r : out_est / (double)P) * 1.15 + 4096.0;
-        int part = (cap_part[1] > done[1].out_count && (double)(cap_part[1] - done[1].out_count) >= expect) ? 1 : 0;
-        if (part == 0 && cap_part[0] <= done[0].out_count) part = 1;
-        for (int redo = 0;; ++redo) {
-          TW_LAUNCH(c, launch_clear(c->table.ptr, slice_bytes, nullptr, c->stream));
-          if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
-          for (int ip = 0; ip < 2; ++ip) {
-            if (!in_cnt[ip]) continue;
-            ExpandLaunch a;
-            a.kc = kc;
-            a.in_keys = in_part[ip];
-            a.n_in = in_cnt[ip];
-            a.adj = small_at(c, L.adj);
-            a.n = n;
-            a.k = k;
-            a.table = c->table.ptr;
-            a.table_slots = slice_slots;
-            a.max_probes = max_probes;
-            a.out_keys = out_part[part];
-            a.out_pred = nullptr;
-            a.out_cap = cap_part[part];
-            a.ctr = d_ctr[part];
-            a.block_threads = 128;
-            a.grid = 0;
-            a.allowed[0] = c->allowed[0];
-            a.allowed[1] = c->allowed[1];
-            a.mmw = 0;
-            a.ranges = P;
-            a.range = r;
-            TW_LAUNCH(c, launch_expand(a, c->stream));
-            ++launches;
-          }
-          if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
-          TW_CK(cudaMemcpyAsync(c->h_ctr, d_ctr[part], sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
-          TW_CK(cudaStreamSynchronize(c->stream));
-          const LevelCounters h = *c->h_ctr;
-          if (timed) {
-            float ms = 0.f;
-            TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-            ms_total += ms;
-          }
-          const unsigned long long got = h.out_count - done[part].out_count;
-          if ((h.overflow & 2u) || got * 100ull > slice_slots * 90ull) {
-            // this range held more than its slice: more states than estimated
-            const double projected = (double)(so_far + got) / (double)(r + 1) * (double)P;
-            out_est = std::max(out_est * 1.25, projected * 1.1);
-            replan = true;
-            break;
-          }
-          if (!(h.overflow & 1u)) {
-            done[part] = h;
-            break;
-          }
-          // the part filled up: undo this pass's counts and redo it into the
-          // other part if that has room for it, else plan the level again
-          TW_CK(cudaMemcpyAsync(d_ctr[part], &done[part], sizeof(LevelCounters), cudaMemcpyHostToDevice,
-                                c->stream));
-          const int other = 1 - part;
-          if (redo == 0 && cap_part[other] > done[other].out_count && cap_part[other] - done[other].out_count >= got) {
-            part = other;
-            continue;
-          }
-          const double projected = (double)(so_far + got) / (double)(r + 1) * (double)P;
-          out_est = std::max(out_est * 1.05, projected * 1.05);
+      for (unsigned long long r = 0; r < P; ++r) {
+        const unsigned long long before = h.out_count;
+        TW_LAUNCH(c, launch_clear(c->table.ptr, slice_bytes, nullptr, c->stream));
+        if (timed) TW_CK(cudaEventRecord(c->ev0, c->stream));
+        for (int ip = 0; ip < 2; ++ip) {
+          if (!in_cnt[ip]) continue;
+          ExpandLaunch a;
+          a.kc = kc;
+          a.in_keys = in_part[ip];
+          a.n_in = in_cnt[ip];
+          a.adj = small_at(c, L.adj);
+          a.n = n;
+          a.k = k;
+          a.table = c->table.ptr;
+          a.table_slots = slice_slots;
+          a.max_probes = max_probes;
+          a.out_keys = out_first;
+          a.out_pred = nullptr;
+          a.out_cap = cap_part[0] + cap_part[1];
+          a.out_tail = out_tail;
+          a.out_split = cap_part[0];
+          a.ctr = c->d_ctr;
+          a.block_threads = 128;
+          a.grid = 0;
+          a.allowed[0] = c->allowed[0];
+          a.allowed[1] = c->allowed[1];
+          a.mmw = 0;
+          a.ranges = P;
+          a.range = r;
+          TW_LAUNCH(c, launch_expand(a, c->stream));
+          ++launches;
+        }
+        if (timed) TW_CK(cudaEventRecord(c->ev1, c->stream));
+        TW_CK(cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(LevelCounters), cudaMemcpyDeviceToHost, c->stream));
+        TW_CK(cudaStreamSynchronize(c->stream));
+        h = *c->h_ctr;
+        if (timed) {
+          float ms = 0.f;
+          TW_CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+          ms_total += ms;
+        }
+        const unsigned long long got = h.out_count - before;
+        if ((h.overflow & 2u) || got * 100ull > slice_slots * 90ull) {
+          // this range held more than its slice: more states than estimated
+          const double projected = (double)h.out_count / (double)(r + 1) * (double)P;
+          out_est = std::max(out_est * 1.25, projected * 1.1);
           replan = true;
           break;
         }
       }
+      // more new sets than the two parts hold: every range was inserted
+      // completely, so the count is exact
+      if (!replan && (h.overflow & 1u)) {
+        out_est = (double)h.out_count * 1.01 + 1024.0;
+        replan = true;
+      }
       if (replan) continue;
       nxt.db = od;
       nxt.off = 0;
-      nxt.dcount = done[0].out_count;
+      nxt.dcount = std::min<unsigned long long>(h.out_count, cap_part[0]);
       nxt.hb = oh;
-      nxt.hcount = done[1].out_count;
-      generated = done[0].generated + done[1].generated;
+      nxt.hcount = h.out_count - nxt.dcount;
+      generated = h.generated;
       R->peak_bytes = std::max<unsigned long long>(R->peak_bytes, total_bytes(c));
       break;
     }
@@ -1076,6 +1059,7 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
   // decide runs in flight at once: k0, k0+1, k0+2 (the sweep from a lower
   // bound usually ends within a few k)
   constexpr int kGroups = 3;
+  static_assert(kGroups <= kFusedMaxGroups, "the fused launch holds at most kFusedMaxGroups groups");
   const int G = std::max(1, std::min(kGroups, k_last - k0 + 1));
   const unsigned long long A =
       c->cfg.fused_states > 0 ? (unsigned long long)c->cfg.fused_states : (1ull << 20);
@@ -1085,7 +1069,7 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
   const size_t kb = ((size_t)A * 8 + 255) & ~size_t(255);
   const size_t pb = ((size_t)A + 255) & ~size_t(255);
   const size_t group_bytes = st_bytes + 2 * tb + kb + pb;
-  const size_t need = (size_t)kFusedMaxGroups * group_bytes;
+  const size_t need = (size_t)kGroups * group_bytes;
   *status = 0;
   if (c->fused.bytes < need) {
     c->fused_clean = false;
@@ -1115,7 +1099,7 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
   f.load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
   f.groups = G;
   for (int j = 0; j < kFusedMaxGroups; ++j) {
-    char* gbase = base + (size_t)j * group_bytes;
+    char* gbase = base + (size_t)std::min(j, kGroups - 1) * group_bytes;
     f.st[j] = reinterpret_cast<FusedState*>(gbase);
     f.table0[j] = gbase + st_bytes;
     f.table1[j] = gbase + st_bytes + tb;
@@ -1130,8 +1114,7 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
   if (!c->fused_clean) {
     // a new buffer, or one a launch left early: empty every group's tables
     // (all ones) once; launches that run to their end leave them empty
-    for (int j = 0; j < kFusedMaxGroups; ++j)
-      TW_CK(cudaMemsetAsync(f.table0[j], 0xff, 2 * tb, c->stream));
+    for (int j = 0; j < kGroups; ++j) TW_CK(cudaMemsetAsync(f.table0[j], 0xff, 2 * tb, c->stream));
     c->fused_clean = true;
   }
   f.tables_clean = 1;

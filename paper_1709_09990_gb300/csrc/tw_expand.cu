@@ -114,6 +114,8 @@ cudaError_t launch_expand_t(const ExpandLaunch& a, cudaStream_t s) {
   p.mmw = a.mmw;
   p.ranges = a.ranges > 0 ? a.ranges : 1;
   p.range = a.range;
+  p.out_tail = static_cast<K*>(a.out_tail);
+  p.out_split = a.out_split;
   if (a.n_in == 0) return cudaSuccess;
   const unsigned long long chunks = (a.n_in + 31ull) / 32ull;
   const unsigned long long blocks_needed = (chunks + kWarps - 1) / kWarps;

@@ -379,6 +379,8 @@ struct LevelOut {
   unsigned long long cap;
   unsigned long long* count;
   unsigned int* overflow;  // bit 0: output full, bit 1: probe limit
+  K* tail = nullptr;       // ranged: positions from split on go to tail[position - split]
+  unsigned long long split = 0;
 };
 
 // Inserts the queued pairs into the table, U per lane at a
@@ -467,7 +469,10 @@ __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, co
         if (st[u] == 2) {
           const unsigned long long o = b + (unsigned long long)__popc(wm[u] & lanemask_lt);
           if (o < out.cap) {
-            kstore_cs(&out.keys[o], key[u]);
+            if (kRanged && out.tail != nullptr && o >= out.split)
+              kstore_cs(&out.tail[o - out.split], key[u]);
+            else
+              kstore_cs(&out.keys[o], key[u]);
             if (kParent)
               __stcs(&out.parent[o], out.parent_base + (uint32_t)src[u]);
             else if (!kRanged)
@@ -517,7 +522,42 @@ struct ExpandParams {
   unsigned long long range;   // and only pairs of this one are inserted (the table is its slice)
   unsigned int group_block = 0, group_blocks = 0;  // a level expanded by a group of a grid's
                                                    // blocks: this block's index in it and its size
+  K* out_tail = nullptr;            // ranged kernels: output positions from out_split on go to
+  unsigned long long out_split = 0;  // out_tail[position - out_split] (a second buffer)
 };
+
+// C(n, r), or cap when it is at least cap.  The products run over
+// min(r, n - r) steps, along which b = C(n - r + j, j) only grows and each
+// division is exact, so with cap <= 2^40 nothing overflows.
+__device__ __forceinline__ unsigned long long binom_capped(int n, int r, unsigned long long cap) {
+  if (r < 0 || r > n) return 0ull;
+  if (r > n - r) r = n - r;
+  unsigned long long b = 1ull;
+  for (int j = 1; j <= r; ++j) {
+    b = b * (unsigned long long)(n - r + j) / (unsigned long long)j;
+    if (b >= cap) return cap;
+  }
+  return b;
+}
+
+// The table of level i -> i+1 of a run whose levels stay below 2^32 sets, in
+// integer arithmetic (the same in every thread): the expected size is cnt
+// times the last growth ratio cnt / prev_cnt clamped to [1/4, n - i] (n at
+// i = 0), plus 25% and 1024, at most the number of sets level i+1 can have;
+// slots = that at load_pct percent, at least 64.
+__device__ __forceinline__ void plan_level(unsigned long long cnt, unsigned long long prev_cnt, int n, int i,
+                                           int load_pct, unsigned long long* table_est, unsigned long long* slots) {
+  const unsigned long long bound =
+      min(cnt * (unsigned long long)(n - i), binom_capped(n, i + 1, 1ull << 40)) + 1ull;
+  unsigned long long est = (unsigned long long)n;
+  if (i > 0) {
+    est = prev_cnt > 0 ? cnt * cnt / prev_cnt : cnt;
+    est = max(est, cnt / 4ull);
+    est = min(est, cnt * (unsigned long long)(n - i));
+  }
+  *table_est = min(est + est / 4ull + 1024ull, bound);
+  *slots = max(64ull, (*table_est * 100ull + (unsigned long long)load_pct - 1ull) / (unsigned long long)load_pct);
+}
 
 // One level i -> i+1 by the whole block: the adjacency rows go to shared
 // memory, then each warp takes chunks of 32 consecutive states (coalesced key
@@ -554,6 +594,8 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   out.cap = p.out_cap;
   out.count = &p.ctr->out_count;
   out.overflow = &p.ctr->overflow;
+  out.tail = p.out_tail;
+  out.split = p.out_split;
   for (unsigned long long chunk = first; chunk < n_chunks; chunk += stride) {
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;

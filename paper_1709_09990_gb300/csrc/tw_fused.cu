@@ -94,13 +94,6 @@ __device__ bool barrier_wait(unsigned int* arrive, unsigned int* gen, unsigned i
   return *(volatile unsigned int*)error == 0u;
 }
 
-__device__ double binom_f(int n, int r) {
-  if (r < 0 || r > n) return 0.0;
-  double b = 1.0;
-  for (int i = 1; i <= r; ++i) b = b * (double)(n - r + i) / (double)i;
-  return b;
-}
-
 template <class K>
 struct FusedArgs {
   const K* adj;                       // n rows in the state layout
@@ -152,18 +145,12 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
   unsigned long long off = 0, cnt = 1, prev_cnt = 0;
   for (int i = 0; i <= n - k - 2; ++i) {
     // the plan of level i -> i+1, the same in every block of the group
-    const double bound = fmin((double)cnt * (double)(n - i), binom_f(n, i + 1)) + 1.0;
-    double est = (double)n;
-    if (i > 0) {
-      double r = prev_cnt > 0 ? (double)cnt / (double)prev_cnt : 1.0;
-      r = fmin(fmax(r, 0.25), (double)(n - i));
-      est = (double)cnt * r;
-    }
-    const double table_est = fmin(est * 1.25 + 1024.0, bound);
-    unsigned long long slots = (unsigned long long)ceil(table_est * 100.0 / (double)a.load_pct);
-    if (slots < 64ull) slots = 64ull;
+    // (integer arithmetic: this part's FP64 rate is a small fraction of its
+    // integer rate)
+    unsigned long long table_est = 0, slots = 0;
+    core::plan_level(cnt, prev_cnt, n, i, a.load_pct, &table_est, &slots);
     const unsigned long long out_off = off + cnt;
-    if (slots > a.table_cap || out_off >= a.arena_cap || (double)(a.arena_cap - out_off) < table_est) return 2;
+    if (slots > a.table_cap || out_off >= a.arena_cap || a.arena_cap - out_off < table_est) return 2;
     const int t = i & 1;
     ExpandParams<K> p;
     p.in_keys = keys + off;
@@ -172,7 +159,6 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
     p.n = n;
     p.k = k;
     p.table = a.table[grp][t];
-    p.table_slots = slots;
     p.max_probes = a.max_probes;
     p.out_keys = keys + out_off;
     p.out_pred = a.pred[grp] + out_off;
@@ -184,22 +170,34 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
     p.range = 0;
     p.group_block = gb;
     p.group_blocks = nb;
-    core::expand_level<K, kFusedWarps, TW_INSERT_UNROLL, false, false, false, true>(p, sAdj, sState, sQueue);
-    // meanwhile empty the table the previous level used
-    for (unsigned long long j = gtid; j < dirty[1 - t]; j += gthreads) a.table[grp][1 - t][j] = kones<K>();
-    dirty[1 - t] = 0;
-    dirty[t] = slots;
-    if (!barrier_wait(&st->arrive, &st->gen, nb, error)) return -2;
-    const LevelCounters& c = st->ctr[i + 1];
-    const unsigned long long got = __ldcg(&c.out_count);
-    const unsigned int ovf = __ldcg(&c.overflow);
-    if (ovf != 0u || got > p.out_cap || got * 100ull > slots * 90ull) return 2;
+    unsigned long long got = 0;
+    for (int attempt = 0;; ++attempt) {
+      p.table_slots = slots;
+      core::expand_level<K, kFusedWarps, TW_INSERT_UNROLL, false, false, false, true>(p, sAdj, sState, sQueue);
+      // meanwhile empty the table the previous level used
+      for (unsigned long long j = gtid; j < dirty[1 - t]; j += gthreads) a.table[grp][1 - t][j] = kones<K>();
+      dirty[1 - t] = 0;
+      dirty[t] = slots;
+      if (!barrier_wait(&st->arrive, &st->gen, nb, error)) return -2;
+      got = __ldcg(&st->ctr[i + 1].out_count);
+      const unsigned int ovf = __ldcg(&st->ctr[i + 1].overflow);
+      if (ovf == 0u) break;  // every pair placed, every new set appended: the level is exact
+      // the arena is full, or the largest table is: the host goes on
+      if ((ovf & 1u) || got > p.out_cap || slots >= a.table_cap || attempt > 0) return 2;
+      // a pair reached the probe limit: run the level again with the largest
+      // table, once every block has read the counters
+      if (!barrier_wait(&st->arrive, &st->gen, nb, error)) return -2;
+      for (unsigned long long j = gtid; j < slots; j += gthreads) a.table[grp][t][j] = kones<K>();
+      if (gb == 0 && threadIdx.x == 0) st->ctr[i + 1] = LevelCounters{};
+      slots = a.table_cap;
+      if (!barrier_wait(&st->arrive, &st->gen, nb, error)) return -2;
+    }
     if (gb == 0 && threadIdx.x == 0) {
       st->level_off[i + 1] = out_off;
       st->level_cnt[i + 1] = got;
       st->run_states += cnt;
       st->run_candidates += cnt * (unsigned long long)(n - i);
-      st->run_generated += __ldcg(&c.generated);
+      st->run_generated += __ldcg(&st->ctr[i + 1].generated);
     }
     prev_cnt = cnt;
     off = out_off;
@@ -262,14 +260,18 @@ __global__ void __launch_bounds__(kFusedWarps * 32, ResidentWarps<K>::value / kF
         break;
       }
       const int r = __ldcg(&a.st[g]->result);
-      ++counted;
       answer_grp = g;  // (the last run read so far: its levels describe a sweep that found no yes)
       answer_last = __ldcg(&a.st[g]->run_last);
+      if (r == 2) {
+        // the host runs this k again from the start: its partial run is not
+        // counted
+        status = 2;
+        answer_k = k;
+        break;
+      }
+      ++counted;
       if (r == 1) {
         status = 1;
-        answer_k = k;
-      } else if (r == 2) {
-        status = 2;
         answer_k = k;
       }
     }
@@ -360,9 +362,10 @@ cudaError_t launch_t(const FusedLaunch& f, cudaStream_t s) {
   if (!coop) return cudaErrorNotSupported;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_solve_kernel<K>, kFusedWarps * 32, 0);
   if (per_sm < 1) return cudaErrorNotSupported;
-  // one block per SM: enough warps for levels of a few thousand states, and
-  // few arrivals per barrier
-  const int grid = sms;
+  // two blocks per SM: each of the three groups has about a hundred blocks
+  // (400 warps, so a level of a few thousand states is one chunk per warp)
+  // and a barrier of a group takes about a hundred arrivals
+  const int grid = sms * (per_sm >= 2 ? 2 : 1);
   if (grid < a.groups) return cudaErrorNotSupported;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fused_solve_kernel<K>), dim3(grid),

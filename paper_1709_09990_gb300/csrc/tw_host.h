@@ -96,7 +96,6 @@ struct tw_ctx {
   // out-of-core decide runs: two pinned, device-mapped host buffers that hold
   // the levels that do not fit the device (reused from run to run)
   HostChunk ooc_host[2] = {{nullptr, nullptr, 0}, {nullptr, nullptr, 0}};
-  LevelCounters* d_ctr_host = nullptr;  // counters of the passes that write to host memory
   // fused small solves: state, two tables and the level arena in one buffer,
   // a pinned mirror of the state, and the graphs whose fused run gave up
   DevBuf fused;

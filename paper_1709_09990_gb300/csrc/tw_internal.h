@@ -47,6 +47,8 @@ struct ExpandLaunch {
   unsigned long long ranges = 0; // > 0: ranged launch - only the pairs whose hash lies in
   unsigned long long range = 0;  // range `range` of `ranges` are inserted, into a table that
                                  // is that range's slice; out_pred is not written
+  void* out_tail = nullptr;      // ranged launch: output positions from out_split on go to
+  unsigned long long out_split = 0;  // out_tail (a second buffer, e.g. in host memory)
 };
 
 cudaError_t launch_expand(const ExpandLaunch& a, cudaStream_t s);
