@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--triage-cap-gb", type=float, default=0.5,
                     help="batch/learned: device cap of the per-graph loop that sorts out the heavy graphs")
     ap.add_argument("--heavy", action="store_true", help="batch: also solve the heavy graphs (default cap)")
+    ap.add_argument("--arena-sweep", action="store_true",
+                    help="batch: also time the persistent kernel with smaller block arenas")
     ap.add_argument("--mem-cap-gb", type=float, default=0.0, help="device memory cap per context (0 = default)")
     ap.add_argument("--spill-levels", action="store_true",
                     help="keep finished levels in pinned host memory (tw_config.spill_levels)")
@@ -687,6 +689,20 @@ def run_batch(args):
     light, loop_tw, loop_states, loop_secs = batch_light(graphs, int(args.triage_cap_gb * (1 << 30)))
     triage_s = time.perf_counter() - t
     rec = batch_arms(graphs, light, loop_tw, loop_secs)
+    if args.arena_sweep:
+        # the persistent kernel with smaller block arenas: graphs that outgrow
+        # one continue in the level-synchronous kernel
+        sub = [graphs[i] for i in light]
+        rec["persistent_by_arena_states"] = {}
+        for A in (1 << 19, 1 << 17, 1 << 15, 1 << 13):
+            with native.Context(device=0, batch_arena_states=A) as c:
+                c.solve_batch(sub[:64])
+                t = time.perf_counter()
+                res = c.solve_batch(sub)
+                dt = time.perf_counter() - t
+            rec["persistent_by_arena_states"][str(A)] = {
+                "seconds": round(dt, 4), "kernel_launches": res["stats"]["kernel_launches"],
+                "same_answers_as_loop": bool(all(int(res["tw"][j]) == loop_tw[i] for j, i in enumerate(light)))}
     heavy = [i for i in range(N) if i not in set(light)]
     out = {"light": rec, "heavy_graphs": len(heavy),
            "heavy_over_triage_cap": sum(1 for i in heavy if loop_tw[i] < 0),

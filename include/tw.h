@@ -148,6 +148,11 @@ typedef struct {
                              are unchanged.                                      */
   int host_cap_mb;        /* out_of_core: pinned host memory, in MB, that levels
                              may occupy; 0 = 85% of the host's physical memory  */
+  int batch_arena_states; /* persistent batched kernel: states each block's arena
+                             holds (a power of two, 4096 .. 2^19; 0 = 2^16, less
+                             when the cap is tight).  A graph whose decide run
+                             outgrows it continues in the level-synchronous
+                             batched kernel.                                     */
   int reserved[1];        /* must be zero                                         */
 } tw_config;
 

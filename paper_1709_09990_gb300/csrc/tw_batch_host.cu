@@ -576,7 +576,15 @@ int run_batch_persistent(tw_ctx* c, const std::vector<HostGraph>& graphs, const 
   // workspace: per block A keys and predecessor bytes, two tables of 2A slots
   const size_t room = c->mem_cap > total_bytes(c) ? c->mem_cap - total_bytes(c) : 0;
   const size_t budget = std::min<size_t>(room / 4, 32ull << 30);
-  unsigned long long A = 1ull << 19;
+  // 2^16 states by default: a graph whose decide runs outgrow that is better
+  // served by the level-synchronous kernel, which spreads each level over the
+  // whole GPU, than by one block (measured on the batch workload's light
+  // graphs: 2^19 1.09 s, 2^17 0.67 s, 2^15 0.56 s, 2^13 0.54 s)
+  unsigned long long A = 1ull << 16;
+  if (c->cfg.batch_arena_states > 0) {
+    A = 1ull << 19;
+    while (A > 4096 && A > (unsigned long long)c->cfg.batch_arena_states) A >>= 1;
+  }
   while (A > 4096 && (size_t)blocks * (A * 41 + 4096) > budget) A >>= 1;
   const unsigned long long T = 2 * A;
   DevMem mem(c);

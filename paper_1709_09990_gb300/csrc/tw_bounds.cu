@@ -25,16 +25,18 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerBlock = 4;
 
 // Warp-wide minimum of (val, idx), lowest idx on ties; idx < 0 means none.
+// One warp reduction of the packed value val << 8 | idx (0 <= val < 2^24,
+// idx < 128) replaces a chain of shuffles: the selection loops of the bounds
+// are sequences of these argmins, so their latency is the kernel's time.
 __device__ __forceinline__ void warp_argmin(int& val, int& idx) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    const int ov = __shfl_xor_sync(kFull, val, d);
-    const int oi = __shfl_xor_sync(kFull, idx, d);
-    const bool take = (oi >= 0) && (idx < 0 || ov < val || (ov == val && oi < idx));
-    if (take) {
-      val = ov;
-      idx = oi;
-    }
+  const unsigned packed = idx < 0 ? 0xffffffffu : ((unsigned)val << 8) | (unsigned)idx;
+  const unsigned m = __reduce_min_sync(kFull, packed);
+  if (m == 0xffffffffu) {
+    val = 1 << 30;
+    idx = -1;
+  } else {
+    val = (int)(m >> 8);
+    idx = (int)(m & 0xffu);
   }
 }
 

@@ -1053,7 +1053,7 @@ bool fused_eligible(const tw_ctx* c, const HostGraph& g) {
 // not run (its buffers do not fit the memory cap).
 // Totals of every run go into st.
 int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, DecideResult* R, int* status,
-              int* answer_k, int* bail_k, tw_stats* st) {
+              int* answer_k, int* bail_k, tw_stats* st, const int32_t* lb_dev) {
   NvtxRange range("tw fused solve n=%d k0=%d", g.n, k0);
   const size_t w = key_bytes(kc);
   // decide runs in flight at once: k0, k0+1, k0+2 (the sweep from a lower
@@ -1098,6 +1098,7 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
   f.max_probes = c->cfg.max_probes > 0 ? c->cfg.max_probes : 256;
   f.load_pct = c->cfg.table_load_pct > 0 ? std::min(90, c->cfg.table_load_pct) : 50;
   f.groups = G;
+  f.lb_dev = lb_dev;
   for (int j = 0; j < kFusedMaxGroups; ++j) {
     char* gbase = base + (size_t)std::min(j, kGroups - 1) * group_bytes;
     f.st[j] = reinterpret_cast<FusedState*>(gbase);
@@ -1129,6 +1130,7 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
   c->fused_clean = h.error == 0u;  // a launch that ran to its end empties the tables it used
   if (h.error) return TW_ERR_TIMEOUT;  // a barrier wait gave up
   *status = h.status;
+  k0 = h.k_start;  // (raised by the device lower bounds when given)
   if (h.status != 1) {
     *bail_k = h.last;
     if (c->fused_skip.size() >= 4096) c->fused_skip.clear();
@@ -1249,7 +1251,7 @@ int decide_graph(tw_ctx* c, const HostGraph& g, int k, int* yes, int32_t* order,
     int status = 0, ans = -1, bail_k = -1;
     tw_stats tmp;
     std::memset(&tmp, 0, sizeof(tmp));
-    rc = run_fused(c, g, kc, k, k, &R, &status, &ans, &bail_k, &tmp);
+    rc = run_fused(c, g, kc, k, k, &R, &status, &ans, &bail_k, &tmp, nullptr);
     if (rc) return rc;
     if (status == 1) {
       if (R.yes && order) {
@@ -1372,6 +1374,25 @@ int bounds_graph(tw_ctx* c, const HostGraph& g, int32_t out[4], bool lower_only)
   return TW_OK;
 }
 
+// Launches the lower bounds (MMD, MMD+) of the uploaded graph into the small
+// buffer's bounds slot without waiting for them; returns their device
+// address.
+int launch_lower_bounds(tw_ctx* c, const HostGraph& g, const int32_t** d_bounds) {
+  SmallLayout L;
+  int32_t* d_out = reinterpret_cast<int32_t*>(small_at(c, L.bounds));
+  int32_t* d_n = d_out + 4;
+  int64_t* d_off = reinterpret_cast<int64_t*>(small_at(c, L.bounds + 64));
+  // (n and the row offset go through the context's pinned counter block)
+  c->h_ctr->out_count = (unsigned long long)(unsigned)g.n;
+  c->h_ctr->generated = 0ull;
+  TW_CK(cudaMemcpyAsync(d_n, &c->h_ctr->out_count, 4, cudaMemcpyHostToDevice, c->stream));
+  TW_CK(cudaMemcpyAsync(d_off, &c->h_ctr->generated, 8, cudaMemcpyHostToDevice, c->stream));
+  TW_LAUNCH(c, launch_bounds(reinterpret_cast<const unsigned long long*>(small_at(c, L.adj64)), d_n, d_off, 1, d_out,
+                             nullptr, c->stream, 1));
+  *d_bounds = d_out;
+  return TW_OK;
+}
+
 int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int32_t* td_parent, uint64_t* td_bags,
                 tw_stats* st, int k_first) {
   NvtxRange range("tw solve n=%d", g.n);
@@ -1381,11 +1402,6 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
   const KeyClass kc = key_class_for(g.n);
   int rc = upload_graph(c, g, kc);
   if (rc) return rc;
-  int32_t b[4];
-  rc = bounds_graph(c, g, b, !c->cfg.ub_shortcut);  // the widths only for the shortcut
-  if (rc) return rc;
-  const int lb = std::max(b[0], b[1]);
-  const int ub = std::min(b[2], b[3]);
   const bool want_walk = order || td_parent || td_bags;
   if (st) {
     st->states_expanded = st->candidates = st->generated = st->peak_frontier_bytes = 0;
@@ -1395,14 +1411,38 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
   }
   int tw = -1;
   DecideResult R;
-  int k0 = std::max(lb, k_first);
+  int k0 = k_first;
   bool fused_done = false;
-  if (c->cfg.ub_shortcut && lb == ub && !want_walk) {
-    tw = ub;
-  } else {
-    if (fused_eligible(c, g)) {
+  bool have_bounds = false;
+  if (!c->cfg.ub_shortcut && fused_eligible(c, g)) {
+    // the fused solve reads the lower bounds on the device: no host round
+    // trip between the bounds and the sweep
+    const int32_t* d_bounds = nullptr;
+    if ((rc = launch_lower_bounds(c, g, &d_bounds))) return rc;
+    int status = 0, ans = -1, bail_k = -1;
+    rc = run_fused(c, g, kc, k_first, g.n - 1, &R, &status, &ans, &bail_k, st, d_bounds);
+    if (rc) return rc;
+    if (status == 1) {
+      tw = ans;
+      fused_done = true;
+    } else if (status == 2) {
+      k0 = bail_k;
+      have_bounds = true;  // (bail_k is at least the lower bound)
+    }
+  }
+  if (!fused_done && !have_bounds) {
+    int32_t b[4];
+    rc = bounds_graph(c, g, b, !c->cfg.ub_shortcut);  // the widths only for the shortcut
+    if (rc) return rc;
+    const int lb = std::max(b[0], b[1]);
+    const int ub = std::min(b[2], b[3]);
+    k0 = std::max(lb, k_first);
+    if (c->cfg.ub_shortcut && lb == ub && !want_walk) {
+      tw = ub;
+      fused_done = true;  // (no decide run and no walk)
+    } else if (c->cfg.ub_shortcut && fused_eligible(c, g)) {
       int status = 0, ans = -1, bail_k = -1;
-      rc = run_fused(c, g, kc, k0, g.n - 1, &R, &status, &ans, &bail_k, st);
+      rc = run_fused(c, g, kc, k0, g.n - 1, &R, &status, &ans, &bail_k, st, nullptr);
       if (rc) return rc;
       if (status == 1) {
         tw = ans;
@@ -1411,6 +1451,8 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
         k0 = bail_k;
       }
     }
+  }
+  {
     for (int k = k0; k < g.n && !fused_done; ++k) {
       rc = decide_with_options(c, g, kc, k, want_walk, &R);
       if (rc) return rc;

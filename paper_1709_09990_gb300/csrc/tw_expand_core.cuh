@@ -540,20 +540,26 @@ __device__ __forceinline__ unsigned long long binom_capped(int n, int r, unsigne
   return b;
 }
 
-// The table of level i -> i+1 of a run whose levels stay below 2^32 sets, in
-// integer arithmetic (the same in every thread): the expected size is cnt
-// times the last growth ratio cnt / prev_cnt clamped to [1/4, n - i] (n at
-// i = 0), plus 25% and 1024, at most the number of sets level i+1 can have;
-// slots = that at load_pct percent, at least 64.
+// The table of level i -> i+1 without FP64 (slow on this part; the result is
+// the same in every thread): the expected size is cnt times the last growth
+// ratio cnt / prev_cnt clamped to [1/4, n - i] (n at i = 0), plus 25% and
+// 1024, at most the number of sets level i+1 can have; slots = that at
+// load_pct percent, at least 64.  The ratio is exact integer arithmetic below
+// 2^32 sets and single precision above.
 __device__ __forceinline__ void plan_level(unsigned long long cnt, unsigned long long prev_cnt, int n, int i,
                                            int load_pct, unsigned long long* table_est, unsigned long long* slots) {
-  const unsigned long long bound =
-      min(cnt * (unsigned long long)(n - i), binom_capped(n, i + 1, 1ull << 40)) + 1ull;
+  const unsigned long long most = cnt * (unsigned long long)(n - i);
+  const unsigned long long bound = min(most, binom_capped(n, i + 1, 1ull << 40)) + 1ull;
   unsigned long long est = (unsigned long long)n;
   if (i > 0) {
-    est = prev_cnt > 0 ? cnt * cnt / prev_cnt : cnt;
+    if (prev_cnt == 0)
+      est = cnt;
+    else if (cnt < (1ull << 32))
+      est = cnt * cnt / prev_cnt;
+    else
+      est = (unsigned long long)fminf((float)cnt * ((float)cnt / (float)prev_cnt), (float)most);
     est = max(est, cnt / 4ull);
-    est = min(est, cnt * (unsigned long long)(n - i));
+    est = min(est, most);
   }
   *table_est = min(est + est / 4ull + 1024ull, bound);
   *slots = max(64ull, (*table_est * 100ull + (unsigned long long)load_pct - 1ull) / (unsigned long long)load_pct);
@@ -569,8 +575,10 @@ __device__ __forceinline__ void plan_level(unsigned long long cnt, unsigned long
 // chunks in turn): a persistent kernel whose blocks work on different graphs.
 // With kKeysL2 the input keys are read through L2 only: persistent kernels,
 // whose arena other SMs rewrite while stale lines may sit in this SM's L1.
+// With kGroup the level is expanded by a group of the grid's blocks
+// (p.group_block of p.group_blocks) instead of the whole grid.
 template <class K, int kWarps, int U = TW_INSERT_UNROLL, bool kMMW = false, bool kRanged = false,
-          bool kBlockLocal = false, bool kKeysL2 = false>
+          bool kBlockLocal = false, bool kKeysL2 = false, bool kGroup = false>
 __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, K* sState, uint16_t* sQueue) {
   constexpr int kBits = KeyTraits<K>::kBits;
   for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
@@ -582,8 +590,8 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   const K valid = kfirst_n<K>(p.n);
   unsigned long long generated_total = 0;
   const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
-  const unsigned long long blk = p.group_blocks ? p.group_block : blockIdx.x;
-  const unsigned long long nblk = p.group_blocks ? p.group_blocks : gridDim.x;
+  const unsigned long long blk = kGroup ? (unsigned long long)p.group_block : (unsigned long long)blockIdx.x;
+  const unsigned long long nblk = kGroup ? (unsigned long long)p.group_blocks : (unsigned long long)gridDim.x;
   const unsigned long long first = kBlockLocal ? (unsigned long long)warp : blk * kWarps + warp;
   const unsigned long long stride = kBlockLocal ? (unsigned long long)kWarps : nblk * kWarps;
   LevelOut<K, false> out;
@@ -594,8 +602,10 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   out.cap = p.out_cap;
   out.count = &p.ctr->out_count;
   out.overflow = &p.ctr->overflow;
-  out.tail = p.out_tail;
-  out.split = p.out_split;
+  if (kRanged) {
+    out.tail = p.out_tail;
+    out.split = p.out_split;
+  }
   for (unsigned long long chunk = first; chunk < n_chunks; chunk += stride) {
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;
@@ -630,12 +640,31 @@ __device__ __forceinline__ void walk_block(const K* __restrict__ keys, const uin
     const K target = *sWalk;
     __syncthreads();  // every thread has the target before the finder replaces it
     const unsigned long long lo = __ldcg(&level_off[j]), cnt = __ldcg(&level_cnt[j]);
-    for (unsigned long long x = threadIdx.x; x < cnt; x += blockDim.x) {
-      if (kload_cg(&keys[lo + x]) == target && atomicExch(sFound, 1) == 0) {
-        const int v = __ldcg(&pred[lo + x]);
-        order[j - 1] = v;
-        *sWalk = target & ~kbit<K>(v);
+    // the scan issues kWalkU loads per thread before comparing (one L2
+    // round trip per kWalkU keys, not per key) and stops at the batch that
+    // found the set
+    constexpr int kWalkU = 8;
+    for (unsigned long long x0 = 0; x0 < cnt; x0 += (unsigned long long)blockDim.x * kWalkU) {
+      K key[kWalkU];
+#pragma unroll
+      for (int u = 0; u < kWalkU; ++u) {
+        const unsigned long long x = x0 + (unsigned long long)u * blockDim.x + threadIdx.x;
+        key[u] = x < cnt ? kload_cg(&keys[lo + x]) : kzero<K>();
       }
+      bool hit = false;
+#pragma unroll
+      for (int u = 0; u < kWalkU; ++u) {
+        const unsigned long long x = x0 + (unsigned long long)u * blockDim.x + threadIdx.x;
+        if (x < cnt && key[u] == target) {
+          hit = true;
+          if (atomicExch(sFound, 1) == 0) {
+            const int v = __ldcg(&pred[lo + x]);
+            order[j - 1] = v;
+            *sWalk = target & ~kbit<K>(v);
+          }
+        }
+      }
+      if (__syncthreads_or(hit)) break;
     }
     __syncthreads();
   }

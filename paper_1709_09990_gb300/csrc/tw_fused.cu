@@ -99,6 +99,7 @@ struct FusedArgs {
   const K* adj;                       // n rows in the state layout
   const unsigned long long* adj64;    // n rows of words64 words (tree decomposition)
   int n, words64, k0, k_last, max_probes, load_pct, groups, tables_clean;
+  const int32_t* lb_dev;              // or null: lower bounds on the device that raise k0
   K* keys[kFusedMaxGroups];           // per group: level arena
   uint8_t* pred[kFusedMaxGroups];
   unsigned long long arena_cap;
@@ -173,7 +174,8 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
     unsigned long long got = 0;
     for (int attempt = 0;; ++attempt) {
       p.table_slots = slots;
-      core::expand_level<K, kFusedWarps, TW_INSERT_UNROLL, false, false, false, true>(p, sAdj, sState, sQueue);
+      core::expand_level<K, kFusedWarps, TW_INSERT_UNROLL, false, false, false, true, true>(p, sAdj, sState,
+                                                                                           sQueue);
       // meanwhile empty the table the previous level used
       for (unsigned long long j = gtid; j < dirty[1 - t]; j += gthreads) a.table[grp][1 - t][j] = kones<K>();
       dirty[1 - t] = 0;
@@ -237,7 +239,10 @@ __global__ void __launch_bounds__(kFusedWarps * 32, ResidentWarps<K>::value / kF
   // table empty)
   unsigned long long dirty[2] = {a.tables_clean ? 0ull : a.table_cap, a.tables_clean ? 0ull : a.table_cap};
   int status = 0, answer_k = -1, answer_grp = -1, answer_last = 0;
-  for (int k_base = a.k0; status == 0; k_base += a.groups) {
+  int k0 = a.k0;
+  if (a.lb_dev) k0 = max(k0, max(__ldcg(&a.lb_dev[0]), __ldcg(&a.lb_dev[1])));
+  if (blockIdx.x == 0 && threadIdx.x == 0) st0->k_start = k0;
+  for (int k_base = k0; status == 0; k_base += a.groups) {
     if (grp < a.groups) {
       const int k = k_base + grp;
       int result = -1, last = 0;
@@ -342,6 +347,7 @@ cudaError_t launch_t(const FusedLaunch& f, cudaStream_t s) {
   a.load_pct = f.load_pct;
   a.groups = f.groups < 1 ? 1 : (f.groups > kFusedMaxGroups ? kFusedMaxGroups : f.groups);
   a.tables_clean = f.tables_clean;
+  a.lb_dev = f.lb_dev;
   for (int g = 0; g < kFusedMaxGroups; ++g) {
     const int h = g < a.groups ? g : 0;
     a.keys[g] = static_cast<K*>(f.keys[h]);

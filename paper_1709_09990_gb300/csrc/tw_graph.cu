@@ -16,13 +16,6 @@ namespace {
 using core::ExpandParams;
 using core::ResidentWarps;
 
-__device__ double binom_d(int n, int r) {
-  if (r < 0 || r > n) return 0.0;
-  double b = 1.0;
-  for (int i = 1; i <= r; ++i) b = b * (double)(n - r + i) / (double)i;
-  return b;
-}
-
 template <class K>
 __global__ void graph_init_kernel(GraphState* st, K* keys) {
   st->cur = 0;
@@ -68,23 +61,15 @@ __global__ void graph_plan_kernel(GraphState* st, LevelCounters* ctr, unsigned l
     }
   }
   const int i = st->cur;
-  const double cur = (double)st->level_cnt[i];
-  const double bound = fmin(cur * (double)(n - i), binom_d(n, i + 1)) + 1.0;
-  double est = (double)n;
-  if (i > 0) {
-    const double prev = (double)st->level_cnt[i - 1];
-    double r = prev > 0.0 ? cur / prev : 1.0;
-    r = fmin(fmax(r, 0.25), (double)(n - i));
-    est = cur * r;
-  }
-  const double table_est = fmin(est * 1.25 + 1024.0, bound);
-  unsigned long long slots = (unsigned long long)ceil(table_est * 100.0 / (double)load_pct);
-  if (slots < 64ull) slots = 64ull;
+  // (integer plan: a chain of FP64 divisions in one thread costs about ten
+  // microseconds per level on this part)
+  unsigned long long table_est = 0, slots = 0;
+  core::plan_level(st->level_cnt[i], i > 0 ? st->level_cnt[i - 1] : 0ull, n, i, load_pct, &table_est, &slots);
   const unsigned long long out_off = st->level_off[i] + st->level_cnt[i];
   // levels for the partitioned insert, and levels that do not fit, go back
   // to the host loop
   if (slots > table_cap || slots * (unsigned long long)w > direct_table_bytes || out_off >= arena_cap ||
-      (double)(arena_cap - out_off) < table_est) {
+      arena_cap - out_off < table_est) {
     st->bail = 1;
     return;
   }

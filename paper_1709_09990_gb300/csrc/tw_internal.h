@@ -168,6 +168,7 @@ struct FusedState {
   int tw, last, group;                // group 0: the first yes k (-1: none up to k_last), the
                                       // index of the final level of the deciding run and
                                       // the group that ran it
+  int k_start;                        // group 0: the first k of the sweep
 };
 
 struct FusedLaunch {
@@ -177,6 +178,8 @@ struct FusedLaunch {
   int n, words64, k0, k_last, max_probes, load_pct;  // decide runs at k0 .. k_last
   int groups;                         // runs in flight at once: k, k+1, .. (1 .. kFusedMaxGroups)
   int tables_clean;                   // 1: every table slot is empty (the last launch emptied them)
+  const int32_t* lb_dev;              // or null: the sweep starts at max(k0, lb_dev[0], lb_dev[1])
+                                      // (lower bounds written by a kernel earlier on the stream)
   void* keys[kFusedMaxGroups];        // per group: arena of arena_cap states
   uint8_t* pred[kFusedMaxGroups];
   unsigned long long arena_cap;

@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("partition_table_mb", ctypes.c_int), ("mmw_prune", ctypes.c_int),
                 ("spill_levels", ctypes.c_int), ("out_of_core", ctypes.c_int),
                 ("fused_states", ctypes.c_int), ("batch_kernel", ctypes.c_int),
-                ("host_cap_mb", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("host_cap_mb", ctypes.c_int), ("batch_arena_states", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -146,7 +147,7 @@ class Context:
                  autotune: bool = False, clique_skip: bool = False, disjoint_paths: bool = False,
                  partition_table_mb: int = 0, mmw_prune: bool = False, spill_levels: bool = False,
                  out_of_core: bool = False, fused_states: int = 0, batch_kernel: int = 0,
-                 host_cap_mb: int = 0):
+                 host_cap_mb: int = 0, batch_arena_states: int = 0):
         cfg = Config()
         cfg.device = device
         cfg.fingerprints = int(fingerprints)
@@ -168,6 +169,7 @@ class Context:
         cfg.fused_states = int(fused_states)
         cfg.batch_kernel = int(batch_kernel)
         cfg.host_cap_mb = int(host_cap_mb)
+        cfg.batch_arena_states = int(batch_arena_states)
         h = _vp()
         _check(lib().tw_create(ctypes.byref(h), ctypes.byref(cfg)), "tw_create")
         self._h = h

@@ -103,9 +103,10 @@ def test_persistent_batch_equals_level_synchronous_and_loop():
                 assert sorted(order) == list(range(len(adj)))
                 assert oracle.width_elim(adj, order) == loop[g]
                 pos += len(adj)
-    # graphs whose levels stay small never leave the persistent kernel: the
-    # bounds and one launch for the whole batch
-    small = [gg.mixed_graph(6000 + j, 10, 20, j % 2 == 0) for j in range(200)]
+    # graphs whose decide runs fit a block's arena never leave the persistent
+    # kernel: the bounds and one launch for the whole batch (n <= 16: a run
+    # holds fewer than 2^16 sets, the default arena)
+    small = [gg.mixed_graph(6000 + j, 10, 16, j % 2 == 0) for j in range(200)]
     with context() as ctx, context(batch_kernel=1) as sync:
         a = ctx.solve_batch(small)
         b = sync.solve_batch(small)
