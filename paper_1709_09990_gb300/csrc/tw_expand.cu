@@ -51,17 +51,29 @@ __global__ void __launch_bounds__(kWarps * 32, ResidentWarps<K>::value / kWarps)
   core::expand_level<K, kWarps, U, kMMW, kRanged>(p, sAdj, sState, sQueue);
 }
 
-// A ranged launch (one hash range of a level whose table is built slice by
-// slice): 4 warps per block, one block per SM slot.
+// One hash range of a level whose table is built slice by slice; the output
+// list may continue in a second buffer (out_tail from position out_split on).
 template <class K, int U>
-cudaError_t launch_ranged(const ExpandParams<K>& p, unsigned long long blocks_needed, cudaStream_t s) {
+__global__ void __launch_bounds__(4 * 32, ResidentWarps<K>::value / 4)
+    expand_ranged_kernel(const ExpandParams<K> p, K* out_tail, unsigned long long out_split) {
+  constexpr int kBits = KeyTraits<K>::kBits;
+  __shared__ K sAdj[kBits];
+  __shared__ K sState[4 * 32];
+  __shared__ uint16_t sQueue[4 * 32 * kBits];
+  core::expand_level<K, 4, U, false, true>(p, sAdj, sState, sQueue, 0u, 0u, out_tail, out_split);
+}
+
+// A ranged launch: 4 warps per block, one block per SM slot.
+template <class K, int U>
+cudaError_t launch_ranged(const ExpandParams<K>& p, K* out_tail, unsigned long long out_split,
+                          unsigned long long blocks_needed, cudaStream_t s) {
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_insert_kernel<K, 4, U, false, true>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_ranged_kernel<K, U>, 128, 0);
   unsigned long long grid = (unsigned long long)sms * (per_sm > 0 ? per_sm : 1);
   if (grid > blocks_needed) grid = blocks_needed;
-  expand_insert_kernel<K, 4, U, false, true><<<(int)grid, 128, 0, s>>>(p);
+  expand_ranged_kernel<K, U><<<(int)grid, 128, 0, s>>>(p, out_tail, out_split);
   return cudaGetLastError();
 }
 
@@ -114,15 +126,15 @@ cudaError_t launch_expand_t(const ExpandLaunch& a, cudaStream_t s) {
   p.mmw = a.mmw;
   p.ranges = a.ranges > 0 ? a.ranges : 1;
   p.range = a.range;
-  p.out_tail = static_cast<K*>(a.out_tail);
-  p.out_split = a.out_split;
   if (a.n_in == 0) return cudaSuccess;
   const unsigned long long chunks = (a.n_in + 31ull) / 32ull;
   const unsigned long long blocks_needed = (chunks + kWarps - 1) / kWarps;
   if (a.ranges > 0) {
     const unsigned long long need4 = (chunks + 3) / 4;
-    if (a.table_slots * sizeof(K) > core::kDeepTableBytes) return launch_ranged<K, 2 * TW_INSERT_UNROLL>(p, need4, s);
-    return launch_ranged<K, TW_INSERT_UNROLL>(p, need4, s);
+    K* tail = static_cast<K*>(a.out_tail);
+    if (a.table_slots * sizeof(K) > core::kDeepTableBytes)
+      return launch_ranged<K, 2 * TW_INSERT_UNROLL>(p, tail, a.out_split, need4, s);
+    return launch_ranged<K, TW_INSERT_UNROLL>(p, tail, a.out_split, need4, s);
   }
   if (a.mmw) {
     // minor-min-width pruning (opt-in): its own instantiation, 4 warps

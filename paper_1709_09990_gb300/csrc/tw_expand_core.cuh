@@ -379,8 +379,6 @@ struct LevelOut {
   unsigned long long cap;
   unsigned long long* count;
   unsigned int* overflow;  // bit 0: output full, bit 1: probe limit
-  K* tail = nullptr;       // ranged: positions from split on go to tail[position - split]
-  unsigned long long split = 0;
 };
 
 // Inserts the queued pairs into the table, U per lane at a
@@ -391,12 +389,15 @@ struct LevelOut {
 //
 // With kRanged the table is the slice of one hash range (in_hash_range): the
 // home slot spreads the range's hashes over the slice (the high word of
-// (hash * ranges mod 2^64) * slots), and no predecessor is stored.
+// (hash * ranges mod 2^64) * slots), no predecessor is stored, and output
+// positions from split on go to tail[position - split] when tail is given (a
+// list continued in a second buffer).
 template <class K, bool kParent, int U = TW_INSERT_UNROLL, bool kRanged = false>
 __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, const K* __restrict__ sS,
                                              const int total, const int lane, K* __restrict__ table,
                                              const unsigned long long slots, const int max_probes,
-                                             const LevelOut<K, kParent>& out, const unsigned long long ranges = 1) {
+                                             const LevelOut<K, kParent>& out, const unsigned long long ranges = 1,
+                                             K* tail = nullptr, const unsigned long long split = 0) {
   const K empty = kones<K>();
   const unsigned lanemask_lt = (1u << lane) - 1u;
   for (int base = 0; base < total; base += 32 * U) {
@@ -469,8 +470,8 @@ __device__ __forceinline__ void insert_queue(const uint16_t* __restrict__ sQ, co
         if (st[u] == 2) {
           const unsigned long long o = b + (unsigned long long)__popc(wm[u] & lanemask_lt);
           if (o < out.cap) {
-            if (kRanged && out.tail != nullptr && o >= out.split)
-              kstore_cs(&out.tail[o - out.split], key[u]);
+            if (kRanged && tail != nullptr && o >= split)
+              kstore_cs(&tail[o - split], key[u]);
             else
               kstore_cs(&out.keys[o], key[u]);
             if (kParent)
@@ -520,10 +521,6 @@ struct ExpandParams {
   int mmw;    // 1: minor-min-width pruning of the states before they are extended
   unsigned long long ranges;  // ranged kernels: the hash space is split in this many ranges,
   unsigned long long range;   // and only pairs of this one are inserted (the table is its slice)
-  unsigned int group_block = 0, group_blocks = 0;  // a level expanded by a group of a grid's
-                                                   // blocks: this block's index in it and its size
-  K* out_tail = nullptr;            // ranged kernels: output positions from out_split on go to
-  unsigned long long out_split = 0;  // out_tail[position - out_split] (a second buffer)
 };
 
 // C(n, r), or cap when it is at least cap.  The products run over
@@ -575,11 +572,14 @@ __device__ __forceinline__ void plan_level(unsigned long long cnt, unsigned long
 // chunks in turn): a persistent kernel whose blocks work on different graphs.
 // With kKeysL2 the input keys are read through L2 only: persistent kernels,
 // whose arena other SMs rewrite while stale lines may sit in this SM's L1.
-// With kGroup the level is expanded by a group of the grid's blocks
-// (p.group_block of p.group_blocks) instead of the whole grid.
+// With kGroup the level is expanded by a group of the grid's blocks (block
+// group_block of group_blocks) instead of the whole grid.  Ranged kernels may
+// continue the output list in out_tail from position out_split on.
 template <class K, int kWarps, int U = TW_INSERT_UNROLL, bool kMMW = false, bool kRanged = false,
           bool kBlockLocal = false, bool kKeysL2 = false, bool kGroup = false>
-__device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, K* sState, uint16_t* sQueue) {
+__device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, K* sState, uint16_t* sQueue,
+                                             const unsigned group_block = 0, const unsigned group_blocks = 0,
+                                             K* out_tail = nullptr, const unsigned long long out_split = 0) {
   constexpr int kBits = KeyTraits<K>::kBits;
   for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
   __syncthreads();
@@ -590,8 +590,8 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   const K valid = kfirst_n<K>(p.n);
   unsigned long long generated_total = 0;
   const unsigned long long n_chunks = (p.n_in + 31ull) / 32ull;
-  const unsigned long long blk = kGroup ? (unsigned long long)p.group_block : (unsigned long long)blockIdx.x;
-  const unsigned long long nblk = kGroup ? (unsigned long long)p.group_blocks : (unsigned long long)gridDim.x;
+  const unsigned long long blk = kGroup ? (unsigned long long)group_block : (unsigned long long)blockIdx.x;
+  const unsigned long long nblk = kGroup ? (unsigned long long)group_blocks : (unsigned long long)gridDim.x;
   const unsigned long long first = kBlockLocal ? (unsigned long long)warp : blk * kWarps + warp;
   const unsigned long long stride = kBlockLocal ? (unsigned long long)kWarps : nblk * kWarps;
   LevelOut<K, false> out;
@@ -602,10 +602,6 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   out.cap = p.out_cap;
   out.count = &p.ctr->out_count;
   out.overflow = &p.ctr->overflow;
-  if (kRanged) {
-    out.tail = p.out_tail;
-    out.split = p.out_split;
-  }
   for (unsigned long long chunk = first; chunk < n_chunks; chunk += stride) {
     const unsigned long long idx = chunk * 32ull + lane;
     const bool active = idx < p.n_in;
@@ -617,7 +613,8 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
     if (kRanged) feas = in_hash_range<K>(S, feas, p.ranges, p.range);
     const int total = build_queue<K>(S, feas, lane, sS, sQ);
     generated_total += (unsigned long long)total;
-    insert_queue<K, false, U, kRanged>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out, p.ranges);
+    insert_queue<K, false, U, kRanged>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out, p.ranges,
+                                       out_tail, out_split);
     __syncwarp();
   }
   if (lane == 0 && generated_total) atomicAdd(&p.ctr->generated, generated_total);

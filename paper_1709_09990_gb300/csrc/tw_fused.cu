@@ -169,13 +169,11 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
     p.mmw = 0;
     p.ranges = 1;
     p.range = 0;
-    p.group_block = gb;
-    p.group_blocks = nb;
     unsigned long long got = 0;
     for (int attempt = 0;; ++attempt) {
       p.table_slots = slots;
       core::expand_level<K, kFusedWarps, TW_INSERT_UNROLL, false, false, false, true, true>(p, sAdj, sState,
-                                                                                           sQueue);
+                                                                                           sQueue, gb, nb);
       // meanwhile empty the table the previous level used
       for (unsigned long long j = gtid; j < dirty[1 - t]; j += gthreads) a.table[grp][1 - t][j] = kones<K>();
       dirty[1 - t] = 0;
