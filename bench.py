@@ -363,6 +363,16 @@ def sub_batch(args, count=512):
             "heavy_graphs": count - len(light), **rec}
 
 
+def sub_learned(args, ntr=2000, nte=200):
+    """A small sample of the learned-k workload: train on `ntr` graphs with n
+    in [12, 40], compare on `nte` held-out graphs with n in [30, 56] (those the
+    per-graph loop solves under the triage cap)."""
+    rec = learned_compare(ntr, nte, int(args.triage_cap_gb * (1 << 30)))
+    rec["workload"] = (f"learned-k sample: train {ntr} graphs n in [12,40] (seeds 1e6+j), test {nte} graphs n in "
+                       "[30,56] (seeds 2e6+j); the full config is --workload learned")
+    return rec
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -462,9 +472,14 @@ def run_ours(args):
            "roofline": roofline, "clocks": clocks}
     if world == 1 and not args.no_sub:
         # the other workloads, after the timed region
-        out["other_workloads"] = {"gnp20": sub_gnp20(stream, max(5, args.steps)),
-                                  "pktree60": sub_pktree60(args),
-                                  "batch": sub_batch(args)}
+        out["other_workloads"] = {}
+        for name, fn in (("gnp20", lambda: sub_gnp20(stream, max(5, args.steps))),
+                         ("pktree60", lambda: sub_pktree60(args)), ("batch", lambda: sub_batch(args)),
+                         ("learned", lambda: sub_learned(args))):
+            try:
+                out["other_workloads"][name] = fn()
+            except Exception as e:  # a failed sub-record must not hide the main line
+                out["other_workloads"][name] = {"error": f"{type(e).__name__}: {e}"}
     ctx.close()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
@@ -723,21 +738,15 @@ def run_batch(args):
 LIGHT_STATES = 1 << 21  # states per solve below which a graph counts as light in the batch report
 
 
-def run_learned(args):
-    """Learned starting bound: label and train on the 20000 training graphs
-    (n in [12, 40]), then solve the 2000 held-out graphs (n in [30, 56]) with
-    proposals (batched) and with the plain per-graph sweep.  Labels come from
-    the batched solve under the triage cap (graphs over it are left out of
-    training); the held-out graphs are sorted by the per-graph loop under the
-    same cap, and the arms are compared on the ones it solves (default cap for
-    the batched arms)."""
+def learned_compare(ntr, nte, tcap):
+    """Label ntr training graphs (batched solve under the triage cap), train
+    the network on the device, then solve the held-out graphs that the
+    per-graph loop solves under that cap with proposals (batched) and with the
+    plain sweep (batched and the loop's own time)."""
     import numpy as np
     from paper_1709_09990_gb300 import graphgen as gg
     from paper_1709_09990_gb300 import learned
     from paper_1709_09990_gb300 import native
-    ntr = args.graphs * 10 if args.graphs else 20000
-    nte = args.graphs or 2000
-    tcap = int(args.triage_cap_gb * (1 << 30))
     tr = [gg.mixed_graph(10**6 + j, 12, 40, j % 2 == 0) for j in range(ntr)]
     te = [gg.mixed_graph(2 * 10**6 + j, 30, 56, j % 2 == 0) for j in range(nte)]
     with native.Context(device=0, mem_cap_bytes=tcap) as small:
@@ -771,20 +780,35 @@ def run_learned(args):
     okl = lk["per_graph_status"] == 0
     ref = np.array([loop_tw[i] for i in solved])
     t_loop = sum(loop_secs[i] for i in solved)
-    _line("time to exact tw, learned-k batched", round(t_learned, 3), "s", args,
+    return {"learned_batch_seconds": round(t_learned, 4), "label_seconds": round(L["seconds"], 2),
+            "train_seconds": round(train_s, 3), "train_graphs_used": int(ok.sum()),
+            "final_train_loss": float(T["loss"][-1]), "offset": off,
+            "test_graphs_compared": len(solved), "test_over_triage_cap": nte - len(solved),
+            "test_solved_learned": int(okl.sum()),
+            "exact_answer_rate": float((lk["tw"][okl] == ref[okl]).mean()) if okl.any() else None,
+            "plain_batch_same_answers": bool((pb["tw"] == ref).all()),
+            "proposal_hits_tw": float((np.rint(hint) == ref).mean()) if len(ref) else None,
+            "plain_loop_seconds": round(t_loop, 4), "plain_batch_seconds": round(t_plain_batch, 4),
+            "speedup_vs_plain_loop": round(t_loop / t_learned, 3) if t_learned else None,
+            "loop_seconds_with_triaged_out_graphs": round(loop_all_s, 3),
+            "decide_runs": {"learned_batch": lk["stats"]["decide_runs"], "plain_batch": pb["stats"]["decide_runs"]}}
+
+
+def run_learned(args):
+    """Learned starting bound: label and train on the 20000 training graphs
+    (n in [12, 40]), then solve the 2000 held-out graphs (n in [30, 56]) with
+    proposals (batched) and with the plain per-graph sweep.  Labels come from
+    the batched solve under the triage cap (graphs over it are left out of
+    training); the held-out graphs are sorted by the per-graph loop under the
+    same cap, and the arms are compared on the ones it solves (default cap for
+    the batched arms)."""
+    ntr = args.graphs * 10 if args.graphs else 20000
+    nte = args.graphs or 2000
+    rec = learned_compare(ntr, nte, int(args.triage_cap_gb * (1 << 30)))
+    _line("time to exact tw, learned-k batched", rec.pop("learned_batch_seconds"), "s", args,
           {"workload": f"train {ntr} graphs n in [12,40] (seeds 1e6+j), test {nte} graphs n in [30,56] "
                        "(seeds 2e6+j), mixed G(n,p) / partial k-trees", "triage_cap_gb": args.triage_cap_gb},
-          {"label_seconds": round(L["seconds"], 2), "train_seconds": round(train_s, 3),
-           "train_graphs_used": int(ok.sum()), "final_train_loss": float(T["loss"][-1]), "offset": off,
-           "test_graphs_compared": len(solved), "test_over_triage_cap": nte - len(solved),
-           "test_solved_learned": int(okl.sum()),
-           "exact_answer_rate": float((lk["tw"][okl] == ref[okl]).mean()) if okl.any() else None,
-           "plain_batch_same_answers": bool((pb["tw"] == ref).all()),
-           "proposal_hits_tw": float((np.rint(hint) == ref).mean()) if len(ref) else None,
-           "plain_loop_seconds": round(t_loop, 3), "plain_batch_seconds": round(t_plain_batch, 3),
-           "speedup_vs_plain_loop": round(t_loop / t_learned, 3) if t_learned else None,
-           "loop_seconds_with_triaged_out_graphs": round(loop_all_s, 3),
-           "decide_runs": {"learned_batch": lk["stats"]["decide_runs"], "plain_batch": pb["stats"]["decide_runs"]}})
+          rec)
 
 
 def main():

@@ -140,6 +140,7 @@ void tw_destroy(tw_ctx* c) {
   }
   if (c->d_gstate) cudaFree(c->d_gstate);
   if (c->h_gstate) cudaFreeHost(c->h_gstate);
+  if (c->h_out) cudaFreeHost(c->h_out);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -1475,11 +1475,8 @@ int solve_graph(tw_ctx* c, const HostGraph& g, int* tw_out, int32_t* order, int3
                       reinterpret_cast<int32_t*>(small_at(c, L.parent)),
                       reinterpret_cast<unsigned long long*>(small_at(c, L.bags)), c->stream));
     }
-    rc = put_from_device(c, order, d_order, (size_t)g.n * 4);
-    if (rc) return rc;
-    rc = put_from_device(c, td_parent, small_at(c, L.parent), (size_t)g.n * 4);
-    if (rc) return rc;
-    rc = put_from_device(c, td_bags, small_at(c, L.bags), (size_t)g.n * g.words * 8);
+    (void)d_order;
+    rc = put_solution(c, g.n, g.words, order, td_parent, td_bags);
     if (rc) return rc;
   }
   TW_CK(cudaStreamSynchronize(c->stream));

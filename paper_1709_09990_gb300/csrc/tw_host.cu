@@ -52,6 +52,41 @@ int put_from_device(tw_ctx* c, void* dst, const void* src_dev, size_t bytes) {
   return TW_OK;
 }
 
+int put_solution(tw_ctx* c, int n, int words, int32_t* order, int32_t* td_parent, uint64_t* td_bags) {
+  SmallLayout L;
+  struct Part {
+    void* dst;
+    size_t off, bytes;
+  } parts[3] = {{order, L.order, (size_t)n * 4},
+                {td_parent, L.parent, (size_t)n * 4},
+                {td_bags, L.bags, (size_t)n * (size_t)words * 8}};
+  bool any_host = false;
+  for (const Part& p : parts) {
+    if (!p.dst) continue;
+    if (is_device_ptr(p.dst))
+      TW_CK(cudaMemcpyAsync(p.dst, small_at(c, p.off), p.bytes, cudaMemcpyDeviceToDevice, c->stream));
+    else
+      any_host = true;
+  }
+  if (any_host) {
+    // the region order .. bags in one copy into the pinned mirror
+    constexpr size_t kRegion = SmallLayout().bounds - SmallLayout().order;
+    if (!c->h_out) {
+      if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_out), kRegion, cudaHostAllocDefault) != cudaSuccess) {
+        c->h_out = nullptr;
+        cudaGetLastError();
+        return TW_ERR_CUDA;
+      }
+    }
+    TW_CK(cudaMemcpyAsync(c->h_out, small_at(c, L.order), kRegion, cudaMemcpyDeviceToHost, c->stream));
+  }
+  TW_CK(cudaStreamSynchronize(c->stream));
+  if (any_host)
+    for (const Part& p : parts)
+      if (p.dst && !is_device_ptr(p.dst)) std::memcpy(p.dst, c->h_out + (p.off - L.order), p.bytes);
+  return TW_OK;
+}
+
 size_t total_bytes(const tw_ctx* c) {
   return c->keys.bytes + c->pred.bytes + c->table.bytes + c->cand_key.bytes + c->cand_v.bytes + c->ooc_keys.bytes;
 }

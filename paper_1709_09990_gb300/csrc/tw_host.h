@@ -101,6 +101,7 @@ struct tw_ctx {
   DevBuf fused;
   bool fused_clean = false;  // every table slot of the fused buffer is empty
   FusedState* h_fused = nullptr;
+  unsigned char* h_out = nullptr;  // pinned mirror of the small buffer's order .. bags region
   std::vector<unsigned long long> fused_skip;
   // options of Section 3.1 for the decide run being prepared
   unsigned long long allowed[2] = {~0ull, ~0ull};
@@ -172,6 +173,10 @@ bool is_device_ptr(const void* p);
 int fetch(void* dst_host, const void* src, size_t bytes);
 int put(tw_ctx* c, void* dst, const void* src_host, size_t bytes);
 int put_from_device(tw_ctx* c, void* dst, const void* src_dev, size_t bytes);
+// The ordering, tree-decomposition parents and bags of a solve from the small
+// buffer into the caller's pointers (each host, device or NULL) with one
+// stream synchronisation.
+int put_solution(tw_ctx* c, int n, int words, int32_t* order, int32_t* td_parent, uint64_t* td_bags);
 size_t total_bytes(const tw_ctx* c);
 int grow(tw_ctx* c, DevBuf* b, size_t need, size_t keep);
 int host_take(tw_ctx* c, size_t bytes, char** out);
