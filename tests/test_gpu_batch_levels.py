@@ -130,3 +130,21 @@ def test_autotuned_persistent_batch_is_exact():
         order = a["orders"][pos: pos + len(adj)].tolist()
         assert oracle.width_elim(adj, order) == int(b["tw"][g])
         pos += len(adj)
+
+
+@pytest.mark.parametrize("arena", [4096, 1 << 19])
+def test_persistent_arena_size_does_not_change_answers(arena):
+    # a small block arena sends most graphs on to the level-synchronous
+    # kernel, a large one keeps them in the persistent kernel; the answers and
+    # the orderings' widths are the same either way
+    graphs = [gg.mixed_graph(8000 + j, 12, 30, j % 2 == 0) for j in range(120)]
+    with context(batch_arena_states=arena) as ctx, context() as ref:
+        a = ctx.solve_batch(graphs)
+        b = ref.solve_batch(graphs)
+    assert a["status"] == 0 and b["status"] == 0
+    assert a["tw"].tolist() == b["tw"].tolist()
+    pos = 0
+    for g, adj in enumerate(graphs):
+        order = a["orders"][pos: pos + len(adj)].tolist()
+        assert oracle.width_elim(adj, order) == int(b["tw"][g])
+        pos += len(adj)
