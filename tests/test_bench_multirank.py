@@ -41,3 +41,18 @@ def test_single_process_is_identity():
     import bench
     assert bench.max_over_ranks(3.0, "cpu") == 3.0
     assert bench.job_throughput(10.0, 1, 2.0) == 5.0
+
+
+def test_host_cap_for_out_of_core_runs():
+    # an explicit --host-cap-gb wins; otherwise 80% of what the process may
+    # use (MemAvailable, or the cgroup limit when lower), in MB
+    import argparse
+    import bench
+    assert bench.host_cap_mb(argparse.Namespace(host_cap_gb=2.5)) == 2560
+    got = bench.host_cap_mb(argparse.Namespace(host_cap_gb=0.0))
+    avail = None
+    for line in open("/proc/meminfo"):
+        if line.startswith("MemAvailable:"):
+            avail = int(line.split()[1]) * 1024
+    if avail:
+        assert 0 < got <= int(0.80 * avail) >> 20
