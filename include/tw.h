@@ -250,7 +250,14 @@ int tw_decide_u32(tw_ctx* ctx, const uint32_t* adj_rows, int n, int k, int* yes,
 int tw_solve(tw_ctx* ctx, const uint64_t* adj, int n, int* tw, int32_t* order,
              int32_t* td_parent, uint64_t* td_bags, tw_stats* st);
 
-/* Many graphs of uneven size in one level-synchronous batched run.
+/* Many graphs of uneven size in one batched run (the Section 3.1 sweep for
+ * each graph).  By default one persistent launch
+ * solves the graphs from a device queue, a block per graph (the whole k sweep,
+ * certification and walk on the device); graphs whose decide runs outgrow a
+ * block's arena (batch_arena_states) continue in level-synchronous steps that
+ * expand the current level of every such graph over the whole GPU, and graphs
+ * that outgrow those, or have n > 64, are solved one at a time
+ * (batch_kernel = 1 uses the level-synchronous steps for every graph).
  *   adj_concat : the graphs' rows concatenated; graph g starts at word
  *                row_offset[g] and has n[g] rows of ceil(n[g]/64) words.
  *   n          : num_graphs vertex counts (1 .. 64 for the batched kernel;
