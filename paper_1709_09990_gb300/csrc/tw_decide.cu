@@ -1067,7 +1067,7 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
   const size_t st_bytes = (sizeof(FusedState) + 255) & ~size_t(255);
   const size_t tb = ((size_t)T * 8 + 255) & ~size_t(255);  // sized for 64-bit states
   const size_t kb = ((size_t)A * 8 + 255) & ~size_t(255);
-  const size_t pb = ((size_t)A * 4 + 255) & ~size_t(255);  // a 32-bit parent index per state
+  const size_t pb = ((size_t)A + 255) & ~size_t(255);
   const size_t group_bytes = st_bytes + 2 * tb + kb + pb;
   const size_t need = (size_t)kGroups * group_bytes;
   *status = 0;
@@ -1105,7 +1105,7 @@ int run_fused(tw_ctx* c, const HostGraph& g, KeyClass kc, int k0, int k_last, De
     f.table0[j] = gbase + st_bytes;
     f.table1[j] = gbase + st_bytes + tb;
     f.keys[j] = gbase + st_bytes + 2 * tb;
-    f.parent_idx[j] = reinterpret_cast<uint32_t*>(gbase + st_bytes + 2 * tb + kb);
+    f.pred[j] = reinterpret_cast<uint8_t*>(gbase + st_bytes + 2 * tb + kb);
   }
   f.arena_cap = A;
   f.table_cap = T;

@@ -574,23 +574,15 @@ __device__ __forceinline__ void plan_level(unsigned long long cnt, unsigned long
 // whose arena other SMs rewrite while stale lines may sit in this SM's L1.
 // With kGroup the level is expanded by a group of the grid's blocks (block
 // group_block of group_blocks) instead of the whole grid.  Ranged kernels may
-// continue the output list in out_tail from position out_split on.  With
-// kParentOut each new set records in out_parent (aligned with the output
-// keys) the index of its parent in the input level instead of the added
-// vertex.  With kAdjLoaded the caller has already put the adjacency rows in
-// sAdj (they do not change between levels).
+// continue the output list in out_tail from position out_split on.
 template <class K, int kWarps, int U = TW_INSERT_UNROLL, bool kMMW = false, bool kRanged = false,
-          bool kBlockLocal = false, bool kKeysL2 = false, bool kGroup = false, bool kParentOut = false,
-          bool kAdjLoaded = false>
+          bool kBlockLocal = false, bool kKeysL2 = false, bool kGroup = false>
 __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, K* sState, uint16_t* sQueue,
                                              const unsigned group_block = 0, const unsigned group_blocks = 0,
-                                             K* out_tail = nullptr, const unsigned long long out_split = 0,
-                                             uint32_t* out_parent = nullptr) {
+                                             K* out_tail = nullptr, const unsigned long long out_split = 0) {
   constexpr int kBits = KeyTraits<K>::kBits;
-  if (!kAdjLoaded) {
-    for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
-    __syncthreads();
-  }
+  for (int i = threadIdx.x; i < p.n; i += blockDim.x) sAdj[i] = p.adj[i];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   K* sS = sState + warp * 32;
@@ -602,10 +594,10 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
   const unsigned long long nblk = kGroup ? (unsigned long long)group_blocks : (unsigned long long)gridDim.x;
   const unsigned long long first = kBlockLocal ? (unsigned long long)warp : blk * kWarps + warp;
   const unsigned long long stride = kBlockLocal ? (unsigned long long)kWarps : nblk * kWarps;
-  LevelOut<K, kParentOut> out;
+  LevelOut<K, false> out;
   out.keys = p.out_keys;
   out.pred = p.out_pred;
-  out.parent = kParentOut ? out_parent : nullptr;
+  out.parent = nullptr;
   out.parent_base = 0;
   out.cap = p.out_cap;
   out.count = &p.ctr->out_count;
@@ -621,9 +613,8 @@ __device__ __forceinline__ void expand_level(const ExpandParams<K>& p, K* sAdj, 
     if (kRanged) feas = in_hash_range<K>(S, feas, p.ranges, p.range);
     const int total = build_queue<K>(S, feas, lane, sS, sQ);
     generated_total += (unsigned long long)total;
-    if (kParentOut) out.parent_base = (uint32_t)(chunk * 32ull);
-    insert_queue<K, kParentOut, U, kRanged>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out,
-                                            p.ranges, out_tail, out_split);
+    insert_queue<K, false, U, kRanged>(sQ, sS, total, lane, p.table, p.table_slots, p.max_probes, out, p.ranges,
+                                       out_tail, out_split);
     __syncwarp();
   }
   if (lane == 0 && generated_total) atomicAdd(&p.ctr->generated, generated_total);
@@ -680,29 +671,6 @@ __device__ __forceinline__ void walk_block(const K* __restrict__ keys, const uin
       if (!ktest(fin, v)) order[pos++] = v;
   }
   __syncthreads();
-}
-
-// The backward walk by one thread over levels that record parent indices:
-// the set at index cur of level j has its parent at index parent[off_j + cur]
-// of level j-1, and the vertex eliminated at step j-1 is the one bit where
-// the two sets differ; then the vertices outside the final set in increasing
-// order.  Level offsets are read through L2 (other blocks wrote them).
-template <class K>
-__device__ __forceinline__ void walk_parents(const K* __restrict__ keys, const uint32_t* __restrict__ parent,
-                                             const unsigned long long* level_off, int last, int n, int32_t* order) {
-  unsigned long long cur = 0;
-  K set = kload_cg(&keys[__ldcg(&level_off[last])]);
-  const K fin = set;
-  for (int j = last; j >= 1; --j) {
-    const unsigned long long pj = __ldcg(&parent[__ldcg(&level_off[j]) + cur]);
-    const K prev = kload_cg(&keys[__ldcg(&level_off[j - 1]) + pj]);
-    order[j - 1] = klowest(set & ~prev);
-    set = prev;
-    cur = pj;
-  }
-  int pos = last;
-  for (int v = 0; v < n; ++v)
-    if (!ktest(fin, v)) order[pos++] = v;
 }
 
 // Tree decomposition from an ordering, by one block (thread per vertex):

@@ -49,30 +49,43 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
 __device__ __forceinline__ void red_add_release(unsigned int* p, unsigned int v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_relaxed(unsigned int* p, unsigned int v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
-// Bounded barrier over `count` co-resident blocks of a cooperative launch, on
-// a counter that only grows: every block calls the barriers of one counter in
-// the same sequence, and barrier number `round` (1, 2, ...) is complete once
-// the counter reaches round * count.  The block's threads meet at a block
-// barrier; its thread 0 arrives with a release add (which publishes the
-// block's writes) and polls the counter with acquire loads, or gives up after
-// kBarrierNs and sets *error.  Returns false once any block has given up.
-__device__ bool barrier_wait(unsigned int* arrive, unsigned int count, unsigned int round, unsigned int* error) {
+// Bounded barrier over `count` co-resident blocks of a cooperative launch,
+// on the counter `arrive` and the generation word `gen`.  The block's threads
+// meet at a block barrier; its thread 0 arrives with an acquire-release add
+// (which also publishes the block's writes); the last block to arrive resets
+// the count and advances the generation with a release; the others poll the
+// generation with acquire loads, or give up after kBarrierNs and set *error.
+// Returns false once any block has given up.
+__device__ bool barrier_wait(unsigned int* arrive, unsigned int* gen, unsigned int count, unsigned int* error) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    red_add_release(arrive, 1u);
-    const unsigned int target = round * count;
-    const unsigned long long t0 = global_ns();
-    unsigned int polls = 0;
-    while (ld_acquire(arrive) < target) {
-      if ((++polls & 255u) == 0u) {
-        if (ld_acquire(error) != 0u) break;
-        if (global_ns() - t0 > kBarrierNs) {
-          atomicExch(error, 1u);
-          break;
+    const unsigned int g = ld_acquire(gen);
+    const unsigned int prev = atom_add_acq_rel(arrive, 1u);
+    if (prev == count - 1) {
+      st_relaxed(arrive, 0u);
+      red_add_release(gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned int polls = 0;
+      while (ld_acquire(gen) == g) {
+        if ((++polls & 255u) == 0u) {
+          if (ld_acquire(error) != 0u) break;
+          if (global_ns() - t0 > kBarrierNs) {
+            atomicExch(error, 1u);
+            break;
+          }
         }
       }
     }
@@ -88,7 +101,7 @@ struct FusedArgs {
   int n, words64, k0, k_last, max_probes, load_pct, groups, tables_clean;
   const int32_t* lb_dev;              // or null: lower bounds on the device that raise k0
   K* keys[kFusedMaxGroups];           // per group: level arena
-  uint32_t* parent_idx[kFusedMaxGroups];  // per group: parent index of every arena state
+  uint8_t* pred[kFusedMaxGroups];
   unsigned long long arena_cap;
   K* table[kFusedMaxGroups][2];
   unsigned long long table_cap;       // slots of each table
@@ -104,8 +117,7 @@ struct FusedArgs {
 // gave up); *last = index of the final level built.
 template <class K>
 __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, unsigned int nb, int k,
-                            unsigned long long dirty[2], unsigned int* round, int* last, K* sAdj, K* sState,
-                            uint16_t* sQueue) {
+                            unsigned long long dirty[2], int* last, K* sAdj, K* sState, uint16_t* sQueue) {
   FusedState* st = a.st[grp];
   unsigned int* error = &a.st[0]->error;
   K* keys = a.keys[grp];
@@ -128,7 +140,7 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
       st->run_states = st->run_candidates = st->run_generated = 0ull;
     }
   }
-  if (!barrier_wait(&st->arrive, nb, ++*round, error)) return -2;
+  if (!barrier_wait(&st->arrive, &st->gen, nb, error)) return -2;
   *last = 0;
   if (k >= n - 1) return 1;
   unsigned long long off = 0, cnt = 1, prev_cnt = 0;
@@ -150,7 +162,7 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
     p.table = a.table[grp][t];
     p.max_probes = a.max_probes;
     p.out_keys = keys + out_off;
-    p.out_pred = nullptr;
+    p.out_pred = a.pred[grp] + out_off;
     p.out_cap = a.arena_cap - out_off;
     p.ctr = &st->ctr[i + 1];
     p.allowed = kones<K>();
@@ -160,13 +172,13 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
     unsigned long long got = 0;
     for (int attempt = 0;; ++attempt) {
       p.table_slots = slots;
-      core::expand_level<K, kFusedWarps, TW_INSERT_UNROLL, false, false, false, true, true, true, true>(
-          p, sAdj, sState, sQueue, gb, nb, nullptr, 0ull, a.parent_idx[grp] + out_off);
+      core::expand_level<K, kFusedWarps, TW_INSERT_UNROLL, false, false, false, true, true>(p, sAdj, sState,
+                                                                                           sQueue, gb, nb);
       // meanwhile empty the table the previous level used
       for (unsigned long long j = gtid; j < dirty[1 - t]; j += gthreads) a.table[grp][1 - t][j] = kones<K>();
       dirty[1 - t] = 0;
       dirty[t] = slots;
-      if (!barrier_wait(&st->arrive, nb, ++*round, error)) return -2;
+      if (!barrier_wait(&st->arrive, &st->gen, nb, error)) return -2;
       got = __ldcg(&st->ctr[i + 1].out_count);
       const unsigned int ovf = __ldcg(&st->ctr[i + 1].overflow);
       if (ovf == 0u) break;  // every pair placed, every new set appended: the level is exact
@@ -174,11 +186,11 @@ __device__ int group_decide(const FusedArgs<K>& a, int grp, unsigned int gb, uns
       if ((ovf & 1u) || got > p.out_cap || slots >= a.table_cap || attempt > 0) return 2;
       // a pair reached the probe limit: run the level again with the largest
       // table, once every block has read the counters
-      if (!barrier_wait(&st->arrive, nb, ++*round, error)) return -2;
+      if (!barrier_wait(&st->arrive, &st->gen, nb, error)) return -2;
       for (unsigned long long j = gtid; j < slots; j += gthreads) a.table[grp][t][j] = kones<K>();
       if (gb == 0 && threadIdx.x == 0) st->ctr[i + 1] = LevelCounters{};
       slots = a.table_cap;
-      if (!barrier_wait(&st->arrive, nb, ++*round, error)) return -2;
+      if (!barrier_wait(&st->arrive, &st->gen, nb, error)) return -2;
     }
     if (gb == 0 && threadIdx.x == 0) {
       st->level_off[i + 1] = out_off;
@@ -215,10 +227,9 @@ __global__ void __launch_bounds__(kFusedWarps * 32, ResidentWarps<K>::value / kF
   __shared__ uint16_t sQueue[kFusedWarps * 32 * kBits];
   __shared__ K128 sTdAdj[128];
   __shared__ int sPos[128];
+  __shared__ K sWalk;
+  __shared__ int sFound;
   FusedState* st0 = a.st[0];
-  // the adjacency rows stay in shared memory for every level of every run
-  for (int i = threadIdx.x; i < a.n; i += blockDim.x) sAdj[i] = a.adj[i];
-  __syncthreads();
   const unsigned int nb = gridDim.x / (unsigned int)a.groups;
   const int grp = (int)(blockIdx.x / nb);  // == groups for the idle remainder
   const unsigned int gb = blockIdx.x % nb;
@@ -226,7 +237,6 @@ __global__ void __launch_bounds__(kFusedWarps * 32, ResidentWarps<K>::value / kF
   // table empty)
   unsigned long long dirty[2] = {a.tables_clean ? 0ull : a.table_cap, a.tables_clean ? 0ull : a.table_cap};
   int status = 0, answer_k = -1, answer_grp = -1, answer_last = 0;
-  unsigned int grp_round = 0, win_round = 0;  // barriers passed, per counter
   int k0 = a.k0;
   if (a.lb_dev) k0 = max(k0, max(__ldcg(&a.lb_dev[0]), __ldcg(&a.lb_dev[1])));
   if (blockIdx.x == 0 && threadIdx.x == 0) st0->k_start = k0;
@@ -235,7 +245,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, ResidentWarps<K>::value / kF
       const int k = k_base + grp;
       int result = -1, last = 0;
       if (k <= a.k_last) {
-        result = group_decide<K>(a, grp, gb, nb, k, dirty, &grp_round, &last, sAdj, sState, sQueue);
+        result = group_decide<K>(a, grp, gb, nb, k, dirty, &last, sAdj, sState, sQueue);
         if (result == -2) return;
       }
       if (gb == 0 && threadIdx.x == 0) {
@@ -243,7 +253,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, ResidentWarps<K>::value / kF
         a.st[grp]->run_last = last;
       }
     }
-    if (!barrier_wait(&st0->w_arrive, gridDim.x, ++win_round, &st0->error)) return;
+    if (!barrier_wait(&st0->w_arrive, &st0->w_gen, gridDim.x, &st0->error)) return;
     // the same decision in every block
     int counted = 0;
     for (int g = 0; g < a.groups && status == 0; ++g) {
@@ -277,7 +287,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, ResidentWarps<K>::value / kF
       }
     }
     // the results are read by every block before the next window overwrites them
-    if (status == 0 && !barrier_wait(&st0->w_arrive, gridDim.x, ++win_round, &st0->error)) return;
+    if (status == 0 && !barrier_wait(&st0->w_arrive, &st0->w_gen, gridDim.x, &st0->error)) return;
   }
   // leave the group's tables empty for the next launch
   if (grp < a.groups) {
@@ -310,10 +320,9 @@ __global__ void __launch_bounds__(kFusedWarps * 32, ResidentWarps<K>::value / kF
   // the backward walk through the answering group's levels, then the tree
   // decomposition
   FusedState* sg = a.st[answer_grp];
-  if (threadIdx.x == 0)
-    core::walk_parents<K>(a.keys[answer_grp], a.parent_idx[answer_grp], sg->level_off, answer_last, a.n, a.order);
+  core::walk_block<K>(a.keys[answer_grp], a.pred[answer_grp], sg->level_off, sg->level_cnt, answer_last, a.n,
+                      a.order, &sWalk, &sFound);
   __threadfence_block();
-  __syncthreads();
   core::td_block(a.adj64, a.n, a.words64, a.order, a.parent, a.bags, sTdAdj, sPos);
   if (threadIdx.x == 0) {
     st0->status = 1;
@@ -340,7 +349,7 @@ cudaError_t launch_t(const FusedLaunch& f, cudaStream_t s) {
   for (int g = 0; g < kFusedMaxGroups; ++g) {
     const int h = g < a.groups ? g : 0;
     a.keys[g] = static_cast<K*>(f.keys[h]);
-    a.parent_idx[g] = f.parent_idx[h];
+    a.pred[g] = f.pred[h];
     a.table[g][0] = static_cast<K*>(f.table0[h]);
     a.table[g][1] = static_cast<K*>(f.table1[h]);
     a.st[g] = f.st[h];

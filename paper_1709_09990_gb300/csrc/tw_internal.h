@@ -160,8 +160,8 @@ struct FusedState {
   LevelCounters ctr[130];             // counters of the expansion that built level j
   unsigned long long states_expanded, candidates, generated;  // group 0: over the counted runs
   unsigned long long run_states, run_candidates, run_generated;  // the group's current run
-  unsigned int arrive, error;         // the group's barrier count; error (group 0): a wait gave up
-  unsigned int w_arrive;              // group 0: barrier count of all blocks (end of a window)
+  unsigned int arrive, gen, error;    // the group's barrier; error (group 0): a wait gave up
+  unsigned int w_arrive, w_gen;       // group 0: barrier of all blocks at the end of a window
   int result, run_last;               // the group's run: 0 no, 1 yes, 2 gave up, -1 not run;
                                       // index of its final level
   int status;                         // group 0: 1 finished, 2 gave up at k = last
@@ -181,7 +181,7 @@ struct FusedLaunch {
   const int32_t* lb_dev;              // or null: the sweep starts at max(k0, lb_dev[0], lb_dev[1])
                                       // (lower bounds written by a kernel earlier on the stream)
   void* keys[kFusedMaxGroups];        // per group: arena of arena_cap states
-  uint32_t* parent_idx[kFusedMaxGroups];  // per group: parent index of every arena state
+  uint8_t* pred[kFusedMaxGroups];
   unsigned long long arena_cap;
   void* table0[kFusedMaxGroups];      // per group: two tables of table_cap slots
   void* table1[kFusedMaxGroups];
